@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Throughput of the FFT-beamforming hot path on the CHIME-like 4x256 workload.
+
+One step = the whole hot path over one integration block of the workload:
+  49152 samples x 1024 channels x 2 pols of a 4x256 int4+4 lattice (1.03e11 antenna
+  samples), as 16 fftbf_execute calls of 3072 samples (8 windows of 384) over a
+  device-resident block, then fftbf_tied_beams for 2048 pointings over the 128 windows.
+The 3072-sample device block (6.4 GB, far above the 129 MB L2) is 4 copies of a seeded
+768-sample host block; every call re-reads it from HBM.
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WL = dict(nx=4, ny=256, pad_x=4, pad_y=512, npol=2, nfreq=1024, T=49152, n_int=384,
+          n_tied=2048, seed=2, n_src=3, amp=1.5, sigma=2.5)
+T_HOST = 768          # seeded host block (2 windows)
+T_DEV = 3072          # device block per fftbf_execute call (8 windows)
+METRIC = "antenna-samples/s at 4x256 int4 lattice"
+UNIT = "antenna-samples/s"
+# Algorithmic FP32 work of the plain form per snapshot (one pol, one t, one f), counted
+# with 5 N log2 N per complex FFT: apodisation 6/sample, E-W 4-point DFT 16 adds per
+# column, N-S 512-point transform of 256 inputs as two 256-point FFTs plus 256 twiddle
+# products per E-W beam, detection + accumulation 4 flops per beam.
+FLOPS_PER_SNAPSHOT = 6 * 1024 + 16 * 256 + 4 * (2 * 5 * 256 * 8 + 6 * 256) + 4 * 2048
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def samples_per_step():
+    return WL["T"] * WL["nfreq"] * WL["npol"] * WL["nx"] * WL["ny"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks ----------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.fh = None
+
+    def start(self):
+        try:
+            self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.flush()
+        self.fh.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.fh.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.fh.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- CPU oracle ---------
+def host_block():
+    src = synth.seeded_sources(WL["seed"] + 100, WL["n_src"], WL["amp"])
+    return synth.volts(T_HOST, WL["nfreq"], WL["npol"], WL["nx"], WL["ny"], seed=WL["seed"],
+                       sigma=WL["sigma"], sources=src)
+
+
+def oracle_sample(block, n_chan, chan0=0):
+    """FP64 oracle on one window x n_chan channels x 2 pols; returns (samples, seconds)."""
+    import oracle
+    w = synth.separable_weights(synth.half_sine(WL["nx"]), synth.half_sine(WL["ny"]))
+    v = np.ascontiguousarray(block[:WL["n_int"], chan0:chan0 + n_chan])
+    t0 = time.perf_counter()
+    oracle.beams(v, WL["nx"], WL["ny"], WL["pad_x"], WL["pad_y"], WL["npol"], n_chan,
+                 WL["n_int"], weights=w.astype(np.complex128))
+    dt = time.perf_counter() - t0
+    return v.size, dt
+
+
+def cpu_cores():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max((i.get("num_threads", 1) for i in info), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(block, budget_s=12.0):
+    n_chan, tot_s, tot_n, used = 2, 0.0, 0, 0
+    chan = 0
+    while tot_s < budget_s and chan + n_chan <= WL["nfreq"]:
+        n, dt = oracle_sample(block, n_chan, chan)
+        tot_s += dt
+        tot_n += n
+        chan += n_chan
+        used += n_chan
+        n_chan = min(n_chan * 2, 32)
+    return {"value": tot_n / tot_s, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"1 window of 384 samples x {used} channels x 2 pols of the 4x256 "
+                      f"workload ({tot_n:.3g} antenna-samples, {tot_s:.1f} s), FP64 numpy "
+                      "separable direct DFT"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    block = host_block()
+    n_chan = 4
+    for _ in range(args.warmup):
+        oracle_sample(block, n_chan)
+    times, ns = [], 0
+    for k in range(args.steps):
+        n, dt = oracle_sample(block, n_chan, (k * n_chan) % WL["nfreq"])
+        times.append(dt)
+        ns += n
+    val = ns / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4x256 lattice, 2 pols, 1024 channels, 49152 samples, "
+                                   "N-S padded to 512, n_int 384, half-sine weights",
+                       "step_sample": f"1 window x {n_chan} channels x 2 pols per step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"1 window x {n_chan} channels x 2 pols per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm ---------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1710_08591_gb300 as fb
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fb.build()
+    fb.lib()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    t_gen = time.perf_counter()
+    block = host_block()
+    t_gen = time.perf_counter() - t_gen
+    nx, ny, mx, my = WL["nx"], WL["ny"], WL["pad_x"], WL["pad_y"]
+    npol, nfreq, n_int, n_tied = WL["npol"], WL["nfreq"], WL["n_int"], WL["n_tied"]
+    w = synth.separable_weights(synth.half_sine(nx), synth.half_sine(ny))
+    u, v = synth.tied_pointings(WL["seed"] + 1, nfreq, n_tied, nx, ny, mx, my)
+
+    hb = torch.from_numpy(block.reshape(-1))
+    dvol = torch.empty(T_DEV * hb.numel() // T_HOST, dtype=torch.uint8, device=dev)
+    for c in range(T_DEV // T_HOST):
+        dvol[c * hb.numel():(c + 1) * hb.numel()].copy_(hb)
+    nwin = WL["T"] // n_int
+    wpc = T_DEV // n_int                               # windows per execute call
+    ncall = WL["T"] // T_DEV
+    beams = torch.empty((nwin, nfreq, mx, my), device=dev)
+    tied = torch.empty((nwin, nfreq, n_tied), device=dev)
+    plan = fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w)
+    if args.form != "fp32":
+        fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16}[args.form])
+    stream = torch.cuda.current_stream(dev)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(ncall)] for _ in range(args.steps)]
+
+    def step(k=None):
+        for c in range(ncall):
+            if k is not None:
+                ev[k][c][0].record(stream)
+            fb.execute(plan, dvol, T_DEV, beams[c * wpc:(c + 1) * wpc], stream)
+            if k is not None:
+                ev[k][c][1].record(stream)
+        fb.tied_beams(plan, beams, nwin, n_tied, u, v, tied, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    kern_ms = [a.elapsed_time(b) for row in ev for a, b in row]
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = samples_per_step() * world / (ms_step / 1e3)
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        hvol = torch.empty(T_DEV * hb.numel() // T_HOST, dtype=torch.uint8, pin_memory=True)
+        for c in range(T_DEV // T_HOST):
+            hvol[c * hb.numel():(c + 1) * hb.numel()].copy_(hb)
+        hbeams = torch.empty((nwin, nfreq, mx, my), pin_memory=True)
+        htied = torch.empty((nwin, nfreq, n_tied), pin_memory=True)
+        hv, hbn, htn = hvol.numpy(), hbeams.numpy(), htied.numpy()
+
+        def e2e_step():
+            for c in range(ncall):
+                fb.execute_host(plan, hv, T_DEV, hbn[c * wpc:(c + 1) * wpc], n_tied, u, v,
+                                htn[c * wpc:(c + 1) * wpc], stream)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(2):
+            e2e_step()
+        if dist:
+            dist.barrier()
+        e_steps = max(2, min(args.steps, 5))
+        te = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        te = (time.perf_counter() - te) / e_steps
+        if dist:
+            tt = torch.tensor([te], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": samples_per_step() * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(ncall * hv.nbytes),
+               "d2h_bytes_per_step": int(hbn.nbytes + htn.nbytes),
+               "ms_per_step": 1e3 * te, "api": "fftbf_execute_host (pinned host buffers)"}
+
+    # ---- roofline of the dominant kernel (the fused beam kernel)
+    peaks, src = measured_peaks()
+    k_ms = sum(kern_ms) / len(kern_ms)
+    samples_launch = T_DEV * nfreq * npol * nx * ny
+    snaps_launch = T_DEV * nfreq * npol
+    bytes_launch = samples_launch + wpc * nfreq * mx * my * 4
+    if args.form == "fp32":
+        flops = FLOPS_PER_SNAPSHOT * snaps_launch
+        achieved = flops / (k_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "beams_fp32_kernel<4,9>", "ms_per_launch": k_ms,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
+                        "peak_gbs": peaks["hbm_gbs"],
+                        "frac": bytes_launch / (k_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "peak_source": src}}
+    else:
+        roof = {"bound": "tensor", "achieved": None, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(block)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.form == "fp32" else args.form.split("_")[1],
+            "data": "synthetic",
+            "config": {"workload": "4x256 lattice (E-W x N-S), 2 pols, 1024 channels, 49152 "
+                                   "samples per step, int4+4 voltages (sigma 2.5 noise + 3 "
+                                   "plane-wave sources), E-W 4-point DFT, N-S padded to 512, "
+                                   "half-sine weights, n_int 384, 2048 tied beams",
+                       "form": args.form,
+                       "l2": "inputs larger than L2 (6.4 GB block re-read from HBM per call)",
+                       "calls_per_step": f"{ncall} x fftbf_execute(T={T_DEV}) + fftbf_tied_beams",
+                       "host_block_gen_s": round(t_gen, 2),
+                       "parallelism": f"{world} GPU(s), independent channel bands per GPU"},
+            "gpu_launches": (ncall + 1) * args.steps,
+            "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--form", choices=["fp32", "tc_fp16", "tc_bf16"], default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

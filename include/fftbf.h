@@ -1,0 +1,156 @@
+/*
+ * fftbf — FFT beamforming of a regular antenna lattice on one GB300 (sm_103a).
+ *
+ * Method: Masui et al., "Algorithms for FFT Beamforming Radio Interferometers"
+ * (arXiv 1710.08591). The paper is written for a 1-D array; the library applies it on
+ * both axes of an nx (E-W) x ny (N-S) lattice, the separable 2-D extension.
+ *
+ * Units and layouts used by every entry point:
+ *   - A voltage sample is one byte: bits 7..4 = real, bits 3..0 = imaginary, each a
+ *     two's-complement 4-bit integer in [-8, 7]. (The paper fixes no bit layout.)
+ *   - volts   uint8 [T][nfreq][npol][nx][ny], row-major. Each polarisation is a
+ *     separate set of antennas (Section 2, dual-polarisation feeds).
+ *   - beams   float [T / n_int][nfreq][pad_x][pad_y]: the unnormalised integrated
+ *     FFT-beam intensities
+ *        P[j,f,A,B] = sum_{t in window j} sum_p |sum_{ix,iy} w[ix,iy] x[t,f,p,ix,iy]
+ *                      exp(-2 pi i (A ix / pad_x + B iy / pad_y))|^2
+ *     (Eq. fftbeamform with the factorizable beam of Eq. bf; the paper's 1/n_samp,
+ *     1/sqrt(n_ant) and flux-unit factors are left to the caller). Beam A is at
+ *     sin(theta_A) = A lambda / (pad_x d) in natural DFT order (Eq. theta_A): indices
+ *     A >= pad/2 are the negative-angle aliases; there is no fftshift.
+ *   - Padding: pad >= 2n - 1 keeps all the information of the redundancy-stacked
+ *     visibilities (Eq. b2n-1; pad = 2n recommended). pad < n is legal: the feeds are
+ *     co-added cyclically, element A being the sum of feeds with a = A mod pad
+ *     (Section 3.4).
+ *   - Windows are non-overlapping runs of n_int samples starting at t = 0 of each call.
+ *
+ * Ownership: the caller owns every buffer passed in; the plan owns its tables and
+ * scratch. Device pointers are plain CUDA device addresses on the plan's device.
+ *
+ * Asynchrony: entry points taking a stream enqueue work on it and return; their return
+ * value reports argument and launch errors. fftbf_plan_sync waits for the plan's work.
+ *
+ * Errors: every int-returning entry point returns FFTBF_OK (0) or a negative code; the
+ * message of the last error on the calling thread is fftbf_last_error().
+ */
+#ifndef FFTBF_H
+#define FFTBF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fftbf_plan fftbf_plan;
+
+enum fftbf_status {
+  FFTBF_OK = 0,
+  FFTBF_EINVAL = -1,      /* bad argument: null pointer, size, shape or pointing */
+  FFTBF_ENOMEM = -2,      /* a device or pinned-host allocation failed */
+  FFTBF_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+  FFTBF_ETIMEOUT = -4,    /* a bounded device-side wait ran out */
+  FFTBF_EUNSUPPORTED = -5 /* valid request this build does not implement */
+};
+
+enum fftbf_precision {
+  FFTBF_PREC_FP32 = 0,    /* FP32 CUDA-core spatial FFT (default) */
+  FFTBF_PREC_TC_FP16 = 1, /* tensor-core GEMM stages, FP16 operands, FP32 accumulate */
+  FFTBF_PREC_TC_BF16 = 2  /* tensor-core GEMM stages, BF16 operands, FP32 accumulate */
+};
+
+/*
+ * Create a plan on the current CUDA device.
+ *   nx, ny      lattice size, E-W x N-S (>= 1).
+ *   pad_x/pad_y number of FFT beams per axis, M in the paper (>= 1; Eq. fftbeamform).
+ *   npol        polarisations, summed after detection (>= 1).
+ *   nfreq       frequency channels, processed independently (>= 1).
+ *   n_int       samples integrated per output window (>= 1; n_samp of Eq. Vab).
+ *   weights     host pointer to nx*ny complex FP32 apodisation weights, interleaved
+ *               (re, im), [ix][iy] row-major; multiplied into the voltages before the
+ *               spatial DFT (naive windowed beam of Section 4.1; per-feed gains of
+ *               Section 4.3 fit here too). NULL means 1 + 0i everywhere. Copied.
+ * Builds the FP32 twiddle and E-W DFT tables from FP64 on the device. Returns NULL on
+ * error (see fftbf_last_error).
+ */
+fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, int nfreq,
+                              int n_int, const float* weights);
+
+/* Select the arithmetic of fftbf_execute (enum fftbf_precision). FFTBF_EUNSUPPORTED if
+ * the form is not available for this lattice. */
+int fftbf_plan_set_precision(fftbf_plan* plan, int precision);
+
+/*
+ * Integrated FFT-beam intensities for T samples (Eq. fftbeamform, Eq. bf):
+ * unpack -> apodise -> zero-padded (or cyclically folded) 2-D spatial DFT -> |.|^2 ->
+ * sum over polarisation -> sum over each window of n_int samples.
+ *   volts_dev  device uint8 [T][nfreq][npol][nx][ny]; any alignment.
+ *   T          samples; a multiple of n_int (else FFTBF_EINVAL); 0 is a no-op.
+ *   beams_dev  device float [T/n_int][nfreq][pad_x][pad_y]; overwritten.
+ *   stream     cudaStream_t to run on (NULL = legacy default stream).
+ * No complex beam is written to memory: detection and integration are fused into the
+ * transform.
+ */
+int fftbf_execute(fftbf_plan* plan, const uint8_t* volts_dev, int64_t T, float* beams_dev,
+                  void* stream);
+
+/*
+ * Tied-array beams at arbitrary pointings, regridded from FFT-beam intensities
+ * (Eq. bp_max_arbitrary, applied per axis):
+ *   tied[j,f,s] = sum_{A,B} w^A(u[f,s]) w^B(v[f,s]) beams[j,f,A,B],
+ *   w^A(y) = (1/M) sin[(2n-1) pi (y - A/M)] / sin[pi (y - A/M)]   (M >= 2n - 1).
+ * On an axis with pad < 2n - 1 the FFT beams do not carry all of the stacked
+ * visibilities and the formula does not hold; there the pointing must sit on the
+ * FFT-beam grid (y * pad an integer within 1e-9, else FFTBF_EINVAL) and the tied beam
+ * uses that FFT beam itself (Eq. theta_A).
+ *   beams_dev  device float [n_windows][nfreq][pad_x][pad_y] from fftbf_execute.
+ *   n_windows  >= 0;  n_tied >= 1.
+ *   u, v       host double [nfreq][n_tied]: (d_x / lambda_f) sin(theta_x) and
+ *              (d_y / lambda_f) sin(theta_y) per frequency, so chromatic steering is the
+ *              caller's choice. Copied.
+ *   tied_dev   device float [n_windows][nfreq][n_tied]; overwritten.
+ * The weight tables are generated in FP64 on the device, rounded to FP32 and kept in
+ * the plan; a later call with identical u, v and n_tied reuses them.
+ */
+int fftbf_tied_beams(fftbf_plan* plan, const float* beams_dev, int64_t n_windows,
+                     int n_tied, const double* u, const double* v, float* tied_dev,
+                     void* stream);
+
+/*
+ * The same pass as fftbf_execute followed by fftbf_tied_beams, on HOST buffers: the
+ * voltages are copied to the device in window-sized chunks on a copy stream owned by
+ * the plan, overlapped with the transform of the previous chunk on `stream`; the
+ * intensities (and tied beams, if n_tied > 0) are copied back to the host.
+ *   volts_host  host uint8 [T][nfreq][npol][nx][ny]; pinned memory gives overlap.
+ *   beams_host  host float [T/n_int][nfreq][pad_x][pad_y]; written.
+ *   n_tied      0 (no tied beams) or the number of pointings; then u, v as in
+ *               fftbf_tied_beams and tied_host = host float [T/n_int][nfreq][n_tied].
+ * The first call allocates the plan's staging buffers (two chunks of voltages and the
+ * device intensities/tied beams of one call); later calls reuse them, growing them if
+ * a call is larger. Stream-ordered: the host outputs are complete once `stream` (or
+ * fftbf_plan_sync) has been synchronised; the inputs must stay valid until then.
+ */
+int fftbf_execute_host(fftbf_plan* plan, const uint8_t* volts_host, int64_t T,
+                       float* beams_host, int n_tied, const double* u, const double* v,
+                       float* tied_host, void* stream);
+
+/* Wait for all work the plan has enqueued; returns the first device-side error seen
+ * (e.g. FFTBF_ETIMEOUT) and clears it. */
+int fftbf_plan_sync(fftbf_plan* plan);
+
+/* Free the plan after waiting for its work. NULL is a no-op. */
+void fftbf_destroy(fftbf_plan* plan);
+
+/* Message of the last error on the calling thread ("" if none). Owned by the library. */
+const char* fftbf_last_error(void);
+
+/*
+ * Test hook for the bit layout: decode n bytes at in_dev into out_dev (device float,
+ * 2n values: re, im interleaved) with the decoder the kernels use.
+ */
+int fftbf_debug_unpack(const uint8_t* in_dev, int64_t n, float* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTBF_H */

@@ -1,0 +1,214 @@
+"""FFT beamforming of a regular antenna lattice on GB300 (arXiv 1710.08591).
+
+Thin ctypes binding of ``libfftbf.so`` (C ABI in ``include/fftbf.h``). The functions
+keep the C names without the ``fftbf_`` prefix and only marshal arguments: every step
+of the computation runs in the library's CUDA kernels. There is no CPU fallback; if the
+library is missing, :func:`lib` raises.
+
+Device buffers may be passed as torch CUDA tensors or as integer device addresses;
+host buffers as numpy arrays. Streams may be a ``torch.cuda.Stream``, an integer
+``cudaStream_t`` or None (torch's current stream when torch is imported, else the
+legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
+           "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
+           "plan_sync", "destroy", "last_error", "debug_unpack"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
+
+FFTBF_OK = 0
+PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
+_STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FftbfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fftbf {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (in-tree)."""
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfftbf.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_1710_08591_gb300.build() "
+                                   "(the library has no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            c_int, c_i64, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+            L.fftbf_plan_create.restype = vp
+            L.fftbf_plan_create.argtypes = [c_int] * 7 + [vp]
+            L.fftbf_plan_set_precision.restype = c_int
+            L.fftbf_plan_set_precision.argtypes = [vp, c_int]
+            L.fftbf_execute.restype = c_int
+            L.fftbf_execute.argtypes = [vp, vp, c_i64, vp, vp]
+            L.fftbf_tied_beams.restype = c_int
+            L.fftbf_tied_beams.argtypes = [vp, vp, c_i64, c_int, vp, vp, vp, vp]
+            L.fftbf_execute_host.restype = c_int
+            L.fftbf_execute_host.argtypes = [vp, vp, c_i64, vp, c_int, vp, vp, vp, vp]
+            L.fftbf_plan_sync.restype = c_int
+            L.fftbf_plan_sync.argtypes = [vp]
+            L.fftbf_destroy.restype = None
+            L.fftbf_destroy.argtypes = [vp]
+            L.fftbf_last_error.restype = ctypes.c_char_p
+            L.fftbf_last_error.argtypes = []
+            L.fftbf_debug_unpack.restype = c_int
+            L.fftbf_debug_unpack.argtypes = [vp, c_i64, vp, vp]
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().fftbf_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc != FFTBF_OK:
+        raise FftbfError(rc, last_error())
+    return rc
+
+
+def _dptr(x) -> int:
+    """Device address of a torch CUDA tensor, or an int address."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _host_f64(a, n) -> np.ndarray:
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr
+
+
+class Plan:
+    """Owning handle of an ``fftbf_plan``."""
+
+    def __init__(self, nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights=None):
+        w = None
+        if weights is not None:
+            w = np.ascontiguousarray(np.asarray(weights).astype(np.complex64)).reshape(-1)
+            if w.size != nx * ny:
+                raise ValueError("weights must have nx*ny complex entries")
+        self.shape = dict(nx=nx, ny=ny, pad_x=pad_x, pad_y=pad_y, npol=npol, nfreq=nfreq,
+                          n_int=n_int)
+        self._weights = w
+        h = lib().fftbf_plan_create(nx, ny, pad_x, pad_y, npol, nfreq, n_int,
+                                    None if w is None else w.ctypes.data)
+        if not h:
+            raise FftbfError(-1, last_error())
+        self.handle = h
+
+    def __getattr__(self, k):
+        shape = self.__dict__.get("shape")
+        if shape is not None and k in shape:
+            return shape[k]
+        raise AttributeError(k)
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            lib().fftbf_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def plan_create(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights=None) -> Plan:
+    return Plan(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights)
+
+
+def plan_set_precision(plan: Plan, precision: int) -> None:
+    _check(lib().fftbf_plan_set_precision(plan.handle, precision))
+
+
+def execute(plan: Plan, volts, T: int, beams, stream=None) -> None:
+    """Integrated FFT-beam intensities: beams[T/n_int][nfreq][pad_x][pad_y] (device)."""
+    _check(lib().fftbf_execute(plan.handle, _dptr(volts), int(T), _dptr(beams), _stream(stream)))
+
+
+def tied_beams(plan: Plan, beams, n_windows: int, n_tied: int, u, v, tied, stream=None) -> None:
+    """Tied-array beams tied[n_windows][nfreq][n_tied] (device) from FFT-beam intensities."""
+    n = plan.nfreq * n_tied
+    uu, vv = _host_f64(u, n), _host_f64(v, n)
+    _check(lib().fftbf_tied_beams(plan.handle, _dptr(beams), int(n_windows), int(n_tied),
+                                  uu.ctypes.data, vv.ctypes.data, _dptr(tied), _stream(stream)))
+
+
+def execute_host(plan: Plan, volts: np.ndarray, T: int, beams: np.ndarray, n_tied: int = 0,
+                 u=None, v=None, tied: np.ndarray | None = None, stream=None) -> None:
+    """fftbf_execute (+ fftbf_tied_beams) on host numpy buffers; stream-ordered."""
+    for a in (volts, beams) + ((tied,) if n_tied else ()):
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+            raise ValueError("host buffers must be C-contiguous numpy arrays")
+    uu = vv = None
+    if n_tied:
+        n = plan.nfreq * n_tied
+        uu, vv = _host_f64(u, n), _host_f64(v, n)
+    _check(lib().fftbf_execute_host(
+        plan.handle, volts.ctypes.data, int(T), beams.ctypes.data, int(n_tied),
+        None if uu is None else uu.ctypes.data, None if vv is None else vv.ctypes.data,
+        None if tied is None else tied.ctypes.data, _stream(stream)))
+
+
+def plan_sync(plan: Plan) -> None:
+    _check(lib().fftbf_plan_sync(plan.handle))
+
+
+def destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def debug_unpack(inp, n: int, out, stream=None) -> None:
+    _check(lib().fftbf_debug_unpack(_dptr(inp), int(n), _dptr(out), _stream(stream)))

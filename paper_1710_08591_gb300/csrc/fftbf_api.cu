@@ -1,0 +1,200 @@
+// C ABI of the FFT-beamforming library: argument checks, plan tables, dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+namespace fftbf {
+
+static thread_local std::string g_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? FFTBF_ENOMEM : FFTBF_ECUDA;
+  return set_error(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Radix plan of a power-of-two N for the Stockham stages: the small radix (2 or 4) goes
+// first so that the last stage, which keeps its outputs as accumulators, is radix 8.
+static int radix_plan(int n, int* r0) {
+  if (n == 1) { *r0 = 1; return 1; }
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  *r0 = (l % 3 == 1) ? 2 : (l % 3 == 2) ? 4 : 8;
+  return (l % 3 == 0) ? l / 3 : l / 3 + 1;
+}
+
+static void remember_stream(fftbf_plan* p, cudaStream_t st) {
+  if (std::find(p->streams_used.begin(), p->streams_used.end(), st) == p->streams_used.end())
+    p->streams_used.push_back(st);
+}
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() { cudaSetDevice(prev_); }
+
+ private:
+  int prev_ = 0;
+};
+
+}  // namespace fftbf
+
+using namespace fftbf;
+
+extern "C" {
+
+const char* fftbf_last_error(void) { return g_error.c_str(); }
+
+fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, int nfreq,
+                              int n_int, const float* weights) {
+  if (nx < 1 || ny < 1 || pad_x < 1 || pad_y < 1 || npol < 1 || nfreq < 1 || n_int < 1) {
+    set_error(FFTBF_EINVAL, "plan sizes must all be >= 1 (nx=%d ny=%d pad_x=%d pad_y=%d "
+              "npol=%d nfreq=%d n_int=%d)", nx, ny, pad_x, pad_y, npol, nfreq, n_int);
+    return nullptr;
+  }
+  if ((int64_t)nx * ny > 65536 || pad_x > 64 || pad_y > 65536) {
+    set_error(FFTBF_EUNSUPPORTED, "lattice limits: nx*ny <= 65536, pad_x <= 64, pad_y <= 65536");
+    return nullptr;
+  }
+  fftbf_plan* p = new (std::nothrow) fftbf_plan();
+  if (!p) {
+    set_error(FFTBF_ENOMEM, "cannot allocate plan");
+    return nullptr;
+  }
+  p->nx = nx; p->ny = ny; p->mx = pad_x; p->my = pad_y;
+  p->npol = npol; p->nfreq = nfreq; p->n_int = n_int;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+  const int nant = nx * ny;
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_w, sizeof(float2) * nant);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_ex, sizeof(float2) * pad_x * nx);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, sizeof(float2) * pad_y);
+  if (e == cudaSuccess) {
+    if (weights) {
+      e = cudaMemcpy(p->d_w, weights, sizeof(float2) * nant, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float2> ones(nant, make_float2(1.f, 0.f));
+      e = cudaMemcpy(p->d_w, ones.data(), sizeof(float2) * nant, cudaMemcpyHostToDevice);
+    }
+  }
+  if (e != cudaSuccess) {
+    cuda_error(e, "fftbf_plan_create");
+    fftbf_destroy(p);
+    return nullptr;
+  }
+  if (build_tables(nx, pad_x, pad_y, p->d_ex, p->d_tw, 0) != FFTBF_OK ||
+      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    if (e != cudaSuccess) cuda_error(e, "plan tables");
+    fftbf_destroy(p);
+    return nullptr;
+  }
+  return p;
+}
+
+int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  if (prec == FFTBF_PREC_FP32) {
+    p->precision = prec;
+    return FFTBF_OK;
+  }
+  if (prec == FFTBF_PREC_TC_FP16 || prec == FFTBF_PREC_TC_BF16)
+    return set_error(FFTBF_EUNSUPPORTED, "tensor-core form not available in this build");
+  return set_error(FFTBF_EINVAL, "unknown precision %d", prec);
+}
+
+int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, void* stream) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  if (T < 0 || T % p->n_int != 0)
+    return set_error(FFTBF_EINVAL, "T = %lld is not a non-negative multiple of n_int = %d",
+                     (long long)T, p->n_int);
+  if (T == 0) return FFTBF_OK;
+  if (!volts || !beams) return set_error(FFTBF_EINVAL, "null voltage or beam pointer");
+  DeviceGuard g(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BeamArgs a{};
+  a.volts = volts;
+  a.beams = beams;
+  a.w = p->d_w;
+  a.ex = p->d_ex;
+  a.tw = p->d_tw;
+  a.nx = p->nx; a.ny = p->ny; a.mx = p->mx; a.my = p->my;
+  a.npol = p->npol; a.nfreq = p->nfreq; a.n_int = p->n_int;
+  a.nyf = std::min(p->ny, p->my);
+  a.nwin = T / p->n_int;
+  a.ew_dft = (p->mx == p->nx) && (p->mx & (p->mx - 1)) == 0 && p->mx <= 16;
+  const int nsnap = p->n_int * p->npol;
+  int S = kMaxElems / (p->mx * p->my);
+  if (S < 1) S = 1;
+  if (S > nsnap) S = nsnap;
+  a.S = S;
+  if (fp32_fft_supported(p->mx, p->my)) a.nst = radix_plan(p->my, &a.r0);
+  const int rc = launch_beams_fp32(a, p->nsm, st);
+  if (rc == FFTBF_OK) remember_stream(p, st);
+  return rc;
+}
+
+int fftbf_tied_beams(fftbf_plan* p, const float* beams, int64_t n_windows, int n_tied,
+                     const double* u, const double* v, float* tied, void* stream) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  if (n_windows < 0 || n_tied < 1)
+    return set_error(FFTBF_EINVAL, "need n_windows >= 0 and n_tied >= 1");
+  if (!u || !v) return set_error(FFTBF_EINVAL, "null pointing array");
+  if (n_windows > 0 && (!beams || !tied)) return set_error(FFTBF_EINVAL, "null beam pointer");
+  DeviceGuard g(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = tied_prepare(p->tied, p->nx, p->ny, p->mx, p->my, p->nfreq, n_tied, u, v, st);
+  if (rc != FFTBF_OK) return rc;
+  rc = tied_launch(p->tied, beams, n_windows, p->nfreq, p->mx, p->my, tied, st);
+  if (rc == FFTBF_OK) remember_stream(p, st);
+  return rc;
+}
+
+int fftbf_plan_sync(fftbf_plan* p) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  DeviceGuard g(p->device);
+  for (cudaStream_t st : p->streams_used) FFTBF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (p->pipe.copy) FFTBF_CUDA_TRY(cudaStreamSynchronize(p->pipe.copy));
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+void fftbf_destroy(fftbf_plan* p) {
+  if (!p) return;
+  {
+    DeviceGuard g(p->device);
+    for (cudaStream_t st : p->streams_used) cudaStreamSynchronize(st);
+    host_pipe_free(p->pipe);
+    tied_free(p->tied);
+    cudaFree(p->d_w);
+    cudaFree(p->d_ex);
+    cudaFree(p->d_tw);
+  }
+  delete p;
+}
+
+int fftbf_debug_unpack(const uint8_t* in, int64_t n, float* out, void* stream) {
+  if (n < 0) return set_error(FFTBF_EINVAL, "negative length");
+  if (n > 0 && (!in || !out)) return set_error(FFTBF_EINVAL, "null pointer");
+  return launch_debug_unpack(in, n, out, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fftbf.h"
+
+namespace fftbf {
+
+// Thread-local error message plus status code.
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define FFTBF_CUDA_TRY(call)                               \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_error(e_, #call);   \
+  } while (0)
+
+constexpr int kThreads = 256;          // threads per CTA of the FP32 beam kernel
+constexpr int kMaxElems = 4096;        // complex values per CTA iteration (S * Mx * My)
+constexpr int kMaxStages = 16;
+
+// Arguments of the FP32 beam kernels (one launch = one fftbf_execute).
+struct BeamArgs {
+  const uint8_t* volts;   // [T][nfreq][npol][nx][ny]
+  float* beams;           // [nwin][nfreq][mx][my]
+  const float2* w;        // [nx][ny] apodisation weights
+  const float2* ex;       // [mx][nx] E-W DFT matrix exp(-2 pi i (A ix mod mx) / mx)
+  const float2* tw;       // [my] N-S twiddles exp(-2 pi i k / my)
+  int nx, ny, mx, my, npol, nfreq, n_int;
+  int nyf;                // min(ny, my): folded N-S input length
+  int S;                  // snapshots per CTA iteration
+  int nst;                // FFT stages (power-of-two my): r0 first, then radix 8
+  int r0;                 // radix of the first stage (1, 2, 4 or 8)
+  int ew_dft;             // 1 if mx == nx and mx is a power of two (E-W is a plain DFT)
+  int64_t nwin;           // windows in this call
+};
+
+// Launch the FP32 fused beam kernel. Returns FFTBF_OK or an error code.
+int launch_beams_fp32(const BeamArgs& a, int nsm, cudaStream_t st);
+// True if the register-FFT path supports this shape (else the direct-DFT path runs).
+bool fp32_fft_supported(int mx, int my);
+int launch_debug_unpack(const uint8_t* in, int64_t n, float* out, cudaStream_t st);
+// FP64 table builders (device), rounded to FP32.
+int build_tables(int nx, int mx, int my, float2* ex, float2* tw, cudaStream_t st);
+
+// Tied-beam weight tables and regridding GEMM.
+struct TiedTables {
+  int n_tied = 0;
+  std::vector<double> u, v;     // host copies of the pointings the tables were made for
+  std::vector<int> hperm;       // host copy of perm
+  float* wx = nullptr;          // [nfreq][n_tied][mx] in sorted order
+  float* wy = nullptr;          // [nfreq][n_tied][my] in sorted order
+  int* perm = nullptr;          // [nfreq][n_tied] sorted slot -> caller's pointing index
+  double* duv = nullptr;        // device scratch for u, v
+  size_t cap_tied = 0;
+};
+int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int n_tied,
+                 const double* u, const double* v, cudaStream_t st);
+int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
+                int my, float* out, cudaStream_t st);
+void tied_free(TiedTables& tt);
+
+// Staging of fftbf_execute_host: two voltage chunks, device outputs, copy stream.
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t freed[2] = {nullptr, nullptr};
+  uint8_t* stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  float* beams = nullptr;
+  size_t beams_cap = 0;
+  float* tied = nullptr;
+  size_t tied_cap = 0;
+};
+void host_pipe_free(HostPipe& hp);
+
+}  // namespace fftbf
+
+struct fftbf_plan {
+  int device = 0;
+  int nsm = 0;
+  int nx = 0, ny = 0, mx = 0, my = 0, npol = 0, nfreq = 0, n_int = 0;
+  int precision = FFTBF_PREC_FP32;
+  float2* d_w = nullptr;
+  float2* d_ex = nullptr;
+  float2* d_tw = nullptr;
+  fftbf::TiedTables tied;
+  fftbf::HostPipe pipe;
+  std::vector<cudaStream_t> streams_used;
+};
