@@ -335,6 +335,32 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_profile_case(args):
+    """A small case of the timed kernels for ncu: 256 channels x 768 samples (400 MB of
+    voltages, above L2), three fftbf_execute calls and one fftbf_tied_beams call."""
+    import torch
+    import paper_1710_08591_gb300 as fb
+    fb.build()
+    nx, ny, mx, my, npol, n_int = 4, 256, 4, 512, 2, 384
+    nfreq, T, n_tied = 256, 768, 2048
+    src = synth.seeded_sources(WL["seed"] + 100, WL["n_src"], WL["amp"])
+    block = synth.volts(T, nfreq, npol, nx, ny, seed=WL["seed"], sigma=WL["sigma"], sources=src)
+    w = synth.separable_weights(synth.half_sine(nx), synth.half_sine(ny))
+    u, v = synth.tied_pointings(WL["seed"] + 1, nfreq, n_tied, nx, ny, mx, my)
+    dvol = torch.from_numpy(block.reshape(-1)).cuda()
+    beams = torch.empty((T // n_int, nfreq, mx, my), device="cuda")
+    tied = torch.empty((T // n_int, nfreq, n_tied), device="cuda")
+    with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
+        if args.form != "fp32":
+            fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16}[args.form])
+        for _ in range(3):
+            fb.execute(plan, dvol, T, beams)
+        fb.tied_beams(plan, beams, T // n_int, n_tied, u, v, tied)
+        fb.plan_sync(plan)
+    print("profile case done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,7 +370,11 @@ def main():
     ap.add_argument("--form", choices=["fp32", "tc_fp16", "tc_bf16"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a small case of the timed kernels (for ncu) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
