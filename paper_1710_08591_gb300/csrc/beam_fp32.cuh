@@ -150,6 +150,12 @@ template <> struct DftHalf<8> {
   }
 };
 
+// Shared-memory layout of a transform: one float2 of padding after every 16, so the
+// stride-R writes of the first Stockham stage and the stride-16 reads of the next stages
+// fall in distinct banks. A transform of length N occupies N + N/16 slots.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+template <int N> struct Tstride { static constexpr int v = N + (N >> 4); };
+
 // ------------------------------------------------------------ static radix plan --
 // N = 2^LOG2N; the small radix (2 or 4) goes first so the last stage is radix 8.
 template <int LOG2N> struct FftPlan {
@@ -173,6 +179,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, int ntr, int nyf, const f
   constexpr int MAXB = kMaxElems / kThreads / R;
   constexpr int LOG2BPT = LOG2N - LR;              // butterflies per transform = N / R
   constexpr int STEP = LOG2N - LOG2NS - LR;        // twiddle W_N^(r k 2^STEP)
+  constexpr int TS = Tstride<(1 << LOG2N)>::v;
   const int total = ntr << LOG2BPT;
   float2 v[MAXB][R];
 #pragma unroll
@@ -181,15 +188,15 @@ __device__ __forceinline__ void fft_stage(float2* buf, int ntr, int nyf, const f
     if (b < total) {
       const int t = b >> LOG2BPT;
       const int j = b & ((1 << LOG2BPT) - 1);
-      const float2* in = buf + (t << LOG2N);
+      const float2* in = buf + t * TS;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int idx = j + (r << LOG2BPT);
         if (FIRST) {
           if (PRUNE && r >= R / 2) v[i][r] = czero();
-          else v[i][r] = idx < nyf ? in[idx] : czero();
+          else v[i][r] = idx < nyf ? in[pad16(idx)] : czero();
         } else {
-          v[i][r] = in[idx];
+          v[i][r] = in[pad16(idx)];
         }
       }
       if (!FIRST) {
@@ -221,9 +228,9 @@ __device__ __forceinline__ void fft_stage(float2* buf, int ntr, int nyf, const f
       const int j = b & ((1 << LOG2BPT) - 1);
       const int k = j & ((1 << LOG2NS) - 1);
       const int d = ((j >> LOG2NS) << (LOG2NS + LR)) + k;
-      float2* out = buf + (t << LOG2N) + d;
+      float2* out = buf + t * TS;
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[r << LOG2NS] = v[i][r];
+      for (int r = 0; r < R; ++r) out[pad16(d + (r << LOG2NS))] = v[i][r];
     }
   }
   __syncthreads();
@@ -293,9 +300,10 @@ __device__ __forceinline__ void stage_bytes(const BeamArgs& a, uint8_t* raw, int
 
 // ------------------------------------------------------------ fused FFT kernel --
 template <int MX, int LOG2N>
-__global__ void __launch_bounds__(kThreads, 2) beams_fp32_kernel(const BeamArgs a) {
+__global__ void __launch_bounds__(kThreads, FFTBF_FP32_MIN_BLOCKS) beams_fp32_kernel(const BeamArgs a) {
   using P = FftPlan<LOG2N>;
   constexpr int N = P::N;
+  constexpr int TS = Tstride<N>::v;
   extern __shared__ __align__(16) unsigned char smem[];
   const int nant = a.nx * a.ny;
   const int rawsz = (a.S * nant + 15) & ~15;
@@ -320,9 +328,10 @@ __global__ void __launch_bounds__(kThreads, 2) beams_fp32_kernel(const BeamArgs 
   stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
   cp_async_commit();
 
-  float acc[16];
+  constexpr int NACC = kMaxElems / kThreads;
+  float acc[NACC];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
 
   while (true) {
     int64_t nitem = item;
@@ -336,39 +345,46 @@ __global__ void __launch_bounds__(kThreads, 2) beams_fp32_kernel(const BeamArgs 
 
     // ---- unpack x weight, N-S fold, E-W transform -> Z[s][A][iyf] in buf
     const uint8_t* raw = smem + cur * rawsz;
-    const int ncol = a.S * a.nyf;
+    // columns (s, iyf); no integer division when a row of columns spans the CTA
+    const bool rows = a.nyf >= kThreads;
+    const int ncol = rows ? a.S * kThreads : a.S * a.nyf;
     for (int c = threadIdx.x; c < ncol; c += kThreads) {
-      const int s = c / a.nyf;
-      const int iyf = c - s * a.nyf;
-      float2 z[MX];
+      int s, iyf0, iystep;
+      if (rows) { s = c / kThreads; iyf0 = c - s * kThreads; iystep = kThreads; }
+      else { s = c / a.nyf; iyf0 = c - s * a.nyf; iystep = a.nyf; }
+      const bool live = it * a.S + s < nsnap;
+      const uint8_t* rs = raw + s * nant;
+      for (int iyf = iyf0; iyf < a.nyf; iyf += iystep) {
+        float2 z[MX];
 #pragma unroll
-      for (int A = 0; A < MX; ++A) z[A] = czero();
-      if (it * a.S + s < nsnap) {
-        const uint8_t* rs = raw + s * nant;
-        if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8 || MX == 16) {
-          if (a.ew_dft) {
+        for (int A = 0; A < MX; ++A) z[A] = czero();
+        if (live) {
+          if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8 || MX == 16) {
+            if (a.ew_dft) {
 #pragma unroll
-            for (int ix = 0; ix < MX; ++ix) {
+              for (int ix = 0; ix < MX; ++ix) {
+                float2 col = czero();
+                for (int iy = iyf; iy < a.ny; iy += N)
+                  col = cadd(col, cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy])));
+                z[ix] = col;
+              }
+              Dft<MX>::run(z);
+            }
+          }
+          if (!a.ew_dft) {
+            for (int ix = 0; ix < a.nx; ++ix) {
               float2 col = czero();
               for (int iy = iyf; iy < a.ny; iy += N)
                 col = cadd(col, cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy])));
-              z[ix] = col;
+#pragma unroll
+              for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
             }
-            Dft<MX>::run(z);
           }
         }
-        if (!a.ew_dft) {
-          for (int ix = 0; ix < a.nx; ++ix) {
-            float2 col = czero();
-            for (int iy = iyf; iy < a.ny; iy += N)
-              col = cadd(col, cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy])));
 #pragma unroll
-            for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
-          }
-        }
+        for (int A = 0; A < MX; ++A) buf[(s * MX + A) * TS + pad16(iyf)] = z[A];
+        if (!rows) break;
       }
-#pragma unroll
-      for (int A = 0; A < MX; ++A) buf[(s * MX + A) * N + iyf] = z[A];
     }
     __syncthreads();
 
@@ -383,12 +399,12 @@ __global__ void __launch_bounds__(kThreads, 2) beams_fp32_kernel(const BeamArgs 
       constexpr int LOG2BPT = LOG2N - LRL;
       const int tot = ntr << LOG2BPT;                  // last-stage butterflies in the CTA
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {                   // acc[e]: butterfly e / RL, leg e % RL
+      for (int e = 0; e < NACC; ++e) {                 // acc[e]: butterfly e / RL, leg e % RL
         const int b = threadIdx.x + (e / RL) * kThreads;
         if (e / RL < kMaxElems / kThreads / RL && b < tot) {
           const int t = b >> LOG2BPT;
           const int j = b & ((1 << LOG2BPT) - 1);
-          red[(t << LOG2N) + j + ((e % RL) << LOG2BPT)] = acc[e];
+          red[(t << LOG2N) + j + ((e % RL) << LOG2BPT)] = acc[e];   // unpadded
         }
         acc[e] = 0.f;
       }
@@ -412,8 +428,9 @@ __global__ void __launch_bounds__(kThreads, 2) beams_fp32_kernel(const BeamArgs 
 inline size_t fft_smem_bytes(const BeamArgs& a) {
   const int nant = a.nx * a.ny;
   const size_t rawsz = ((size_t)a.S * nant + 15) & ~(size_t)15;
+  const size_t ts = (size_t)a.my + (a.my >> 4);
   return 2 * rawsz + sizeof(float2) * ((size_t)nant + (size_t)a.mx * a.nx + a.my +
-                                       (size_t)a.S * a.mx * a.my);
+                                       (size_t)a.S * a.mx * ts);
 }
 
 template <int MX, int LOG2N>

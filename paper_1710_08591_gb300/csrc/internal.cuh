@@ -22,7 +22,10 @@ int cuda_error(cudaError_t e, const char* what);
   } while (0)
 
 constexpr int kThreads = 256;          // threads per CTA of the FP32 beam kernel
-constexpr int kMaxElems = 4096;        // complex values per CTA iteration (S * Mx * My)
+#ifndef FFTBF_FP32_MIN_BLOCKS
+#define FFTBF_FP32_MIN_BLOCKS 2            // resident CTAs per SM the register budget targets
+#endif
+constexpr int kMaxElems = 2048;        // complex values per CTA iteration (S * Mx * My)
 constexpr int kMaxStages = 16;
 
 // Arguments of the FP32 beam kernels (one launch = one fftbf_execute).
