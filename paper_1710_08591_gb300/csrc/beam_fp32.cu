@@ -2,9 +2,18 @@
 // shapes, the unpack test hook and the FP64 plan-table builder.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "beam_fp32.cuh"
 
 namespace fftbf {
+
+// Test hook: FFTBF_FP32_GENERIC=1 routes every shape to the generic kernels, so the
+// parity tests can cover both paths on the same inputs.
+static bool getenv_flag(const char* name) {
+  const char* v = getenv(name);
+  return v && v[0] && v[0] != '0';
+}
 
 // ------------------------------------------------------ direct-DFT fallback kernel --
 // Any mx, my (e.g. the M = 2n - 1 minimum padding). One snapshot at a time; thread-owned
@@ -76,6 +85,8 @@ extern template int launch_fft_mx<16>(const BeamArgs&, int, int, cudaStream_t);
 
 int launch_beams_fp32(const BeamArgs& a, int nsm, cudaStream_t st) {
   if (a.nwin <= 0) return FFTBF_OK;
+  if (fp32_n512_supported(a) && !getenv_flag("FFTBF_FP32_GENERIC"))
+    return launch_beams_fp32_n512(a, nsm, st);
   if (fp32_fft_supported(a.mx, a.my) && fft_smem_bytes(a) <= 200 * 1024) {
     int log2n = 0;
     while ((1 << log2n) < a.my) ++log2n;

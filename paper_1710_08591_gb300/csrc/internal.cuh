@@ -48,6 +48,9 @@ struct BeamArgs {
 int launch_beams_fp32(const BeamArgs& a, int nsm, cudaStream_t st);
 // True if the register-FFT path supports this shape (else the direct-DFT path runs).
 bool fp32_fft_supported(int mx, int my);
+// Warp-per-transform kernel for my == 512 with at most 256 feeds on the N-S axis.
+bool fp32_n512_supported(const BeamArgs& a);
+int launch_beams_fp32_n512(const BeamArgs& a, int nsm, cudaStream_t st);
 int launch_debug_unpack(const uint8_t* in, int64_t n, float* out, cudaStream_t st);
 // FP64 table builders (device), rounded to FP32.
 int build_tables(int nx, int mx, int my, float2* ex, float2* tw, cudaStream_t st);

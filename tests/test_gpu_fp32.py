@@ -61,6 +61,10 @@ CASES = [
     (1, 1, 1, 1, 1, 2, 8, 4, "random"),             # one antenna, one beam
     (1, 2, 1, 4, 1, 3, 12, 3, "uniform"),
     (4, 8, 8, 16, 2, 2, 32, 8, "random"),           # E-W padded: not a plain DFT
+    (1, 256, 1, 512, 2, 3, 30, 5, "random"),        # 512-beam kernel, 4 snapshots/step, ragged
+    (2, 200, 2, 512, 1, 2, 14, 7, "half_sine"),     # 512-beam kernel, 200 feeds, ragged
+    (8, 256, 8, 512, 2, 2, 16, 8, "random"),        # 512-beam kernel, 8 warps
+    (3, 256, 4, 512, 2, 2, 16, 8, "random"),        # 512-beam kernel, E-W padded 3 -> 4
 ]
 
 
@@ -74,6 +78,17 @@ def test_beams_match_oracle(case):
     assert np.all(np.isfinite(got))
     err = rel_err_per_beam(got, ref)
     assert err.max() <= TOL_BEAM, f"max rel err {err.max():.3g}"
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] == 512], ids=lambda c: "x".join(map(str, c[:4])))
+def test_generic_kernel_on_512_shapes(case, monkeypatch):
+    """The generic Stockham kernel, forced on shapes the 512-beam kernel normally takes."""
+    monkeypatch.setenv("FFTBF_FP32_GENERIC", "1")
+    nx, ny, mx, my, npol, nfreq, T, n_int, wk = case
+    v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights=wk, seed=4)
+    got = run_beams(v, w, nx, ny, mx, my, npol, nfreq, n_int)
+    ref = oracle_beams(v, w, nx, ny, mx, my, npol, nfreq, n_int)
+    assert rel_err_per_beam(got, ref).max() <= TOL_BEAM
 
 
 def test_tiny_matches_visibility_route():
