@@ -150,6 +150,36 @@ const char* fftbf_last_error(void);
  */
 int fftbf_debug_unpack(const uint8_t* in_dev, int64_t n, float* out_dev, void* stream);
 
+/*
+ * fftbf_execute without a plan and without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, such
+ * as an application that hands all device memory to its own pool before it starts
+ * streaming, or a real-time loop that must not make allocator calls (cudaMalloc and
+ * cudaFree can synchronise the device and stall every stream).
+ *
+ * It computes exactly what fftbf_execute computes, with the same kernels; the small
+ * tables a plan would allocate (E-W DFT matrix, N-S twiddles, and unit weights when
+ * weights_dev is NULL) are written instead into one fixed array of device memory that
+ * the library reserves statically: FFTBF_NOALLOC_SCRATCH_BYTES on every GPU that loads
+ * the library, held until the process exits.
+ *   nx ... n_int  as for fftbf_plan_create; the tables must fit the array:
+ *                 8 * (pad_x*nx + pad_y + (weights_dev ? 0 : nx*ny)) bytes
+ *                 <= FFTBF_NOALLOC_SCRATCH_BYTES, else FFTBF_EINVAL with a message.
+ *   weights_dev   device pointer (8-byte aligned) to nx*ny complex FP32 weights (re, im
+ *                 interleaved, [ix][iy]), or NULL for 1 + 0i; read, not copied.
+ *   volts_dev, T, beams_dev, stream  as for fftbf_execute.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture begins.
+ * Every call rewrites the tables before its transform reads them, so nothing carries
+ * over from the previous call. All calls share the one array: calls whose work
+ * overlaps on the GPU (on different streams, or from several host threads) race on it
+ * and must be serialised by the caller.
+ */
+#define FFTBF_NOALLOC_SCRATCH_BYTES (64 * 1024)
+int fftbf_execute_noalloc(int nx, int ny, int pad_x, int pad_y, int npol, int nfreq,
+                          int n_int, const float* weights_dev, const uint8_t* volts_dev,
+                          int64_t T, float* beams_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

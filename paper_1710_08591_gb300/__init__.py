@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
-           "plan_sync", "destroy", "last_error", "debug_unpack"]
+           "plan_sync", "destroy", "last_error", "debug_unpack", "execute_noalloc"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
             L.fftbf_destroy.argtypes = [vp]
             L.fftbf_last_error.restype = ctypes.c_char_p
             L.fftbf_last_error.argtypes = []
+            L.fftbf_execute_noalloc.restype = c_int
+            L.fftbf_execute_noalloc.argtypes = [c_int] * 7 + [vp, vp, c_i64, vp, vp]
             L.fftbf_debug_unpack.restype = c_int
             L.fftbf_debug_unpack.argtypes = [vp, c_i64, vp, vp]
             _lib = L
@@ -208,6 +210,14 @@ def plan_sync(plan: Plan) -> None:
 
 def destroy(plan: Plan) -> None:
     plan.close()
+
+
+def execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights, volts, T: int, beams,
+                    stream=None) -> None:
+    """fftbf_execute without a plan or any device allocation (tables in static device
+    memory); weights is a device tensor of nx*ny complex64 values or None."""
+    _check(lib().fftbf_execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, _dptr(weights),
+                                       _dptr(volts), int(T), _dptr(beams), _stream(stream)))
 
 
 def debug_unpack(inp, n: int, out, stream=None) -> None:
