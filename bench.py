@@ -40,6 +40,10 @@ UNIT = "antenna-samples/s"
 # products per E-W beam, detection + accumulation 4 flops per beam.
 FLOPS_PER_SNAPSHOT = 6 * 1024 + 16 * 256 + 4 * (2 * 5 * 256 * 8 + 6 * 256) + 4 * 2048
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
+# 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
+# whenever the kernel changes until it is captured again.
+TRAFFIC_FP32 = 16 * (402.788864e6 + 3.653632e6)
 
 
 def samples_per_step():
@@ -296,8 +300,8 @@ def run_ours(args, rank, world, local_rank):
         flops = FLOPS_PER_SNAPSHOT * snaps_launch
         achieved = flops / (k_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "kernel": "beams_fp32_kernel<4,9>", "ms_per_launch": k_ms,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_FP32,
+                "kernel": "beams_fp32_n512_kernel<4>", "ms_per_launch": k_ms,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
                         "peak_gbs": peaks["hbm_gbs"],
