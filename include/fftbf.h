@@ -21,7 +21,7 @@
  *   - Padding: pad >= 2n - 1 keeps all the information of the redundancy-stacked
  *     visibilities (Eq. b2n-1; pad = 2n recommended). pad < n is legal: the feeds are
  *     co-added cyclically, element A being the sum of feeds with a = A mod pad
- *     (Section 3.4).
+ *     (Section 3.2).
  *   - Windows are non-overlapping runs of n_int samples starting at t = 0 of each call.
  *
  * Ownership: the caller owns every buffer passed in; the plan owns its tables and
@@ -69,7 +69,7 @@ enum fftbf_precision {
  *   weights     host pointer to nx*ny complex FP32 apodisation weights, interleaved
  *               (re, im), [ix][iy] row-major; multiplied into the voltages before the
  *               spatial DFT (naive windowed beam of Section 4.1; per-feed gains of
- *               Section 4.3 fit here too). NULL means 1 + 0i everywhere. Copied.
+ *               Section 4.2 fit here too). NULL means 1 + 0i everywhere. Copied.
  * Builds the FP32 twiddle and E-W DFT tables from FP64 on the device. Returns NULL on
  * error (see fftbf_last_error).
  */

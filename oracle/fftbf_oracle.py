@@ -20,7 +20,7 @@ Conventions (the paper is 1-D; the lattice is its separable 2-D extension):
 The paper's normalisations (1/n_samp, 1/sqrt(n_ant), c^2/(k_B nu^2)) are dropped: with
 uniform weights the paper's b_A equals P / (n_samp * n_ant) for one polarisation.
 When M < n on an axis the direct sum folds the feeds cyclically by itself, because
-exp(-2 pi i A a / M) depends only on a mod M (Section 3.4, cyclic co-adding).
+exp(-2 pi i A a / M) depends only on a mod M (Section 3.2, cyclic co-adding).
 """
 from __future__ import annotations
 

@@ -9,7 +9,7 @@
 //      of two, else the folded DFT matrix) -> Z[s][A][iy] in shared memory;
 //   3. N-S transform of length my = 2^LOG2N as mixed-radix Stockham stages in shared
 //      memory, the first stage pruned when half of its inputs are zero padding
-//      (Section 3.4);
+//      (Section 3.2);
 //   4. the last stage keeps its outputs in registers, squares them and adds them to
 //      per-thread accumulators (Eq. bf): no complex beam leaves the SM.
 // At the end of the window the S partial sums are added in a fixed order and written

@@ -75,7 +75,7 @@ def pin_numpy_fft(o, nx=3, ny=5, mx=4, my=16, seed=0):
     got2 = o.field_direct(x, w, mx, my)
     wx = w * x
     grid = np.zeros((2, mx, my), dtype=np.complex128)
-    for ix in range(nx):          # cyclic co-adding when M < n (Section 3.4), padding otherwise
+    for ix in range(nx):          # cyclic co-adding when M < n (Section 3.2), padding otherwise
         for iy in range(ny):
             grid[:, ix % mx, iy % my] += wx[:, ix, iy]
     ref = np.fft.fft2(grid)
