@@ -76,8 +76,14 @@ enum fftbf_precision {
 fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, int nfreq,
                               int n_int, const float* weights);
 
-/* Select the arithmetic of fftbf_execute (enum fftbf_precision). FFTBF_EUNSUPPORTED if
- * the form is not available for this lattice. */
+/*
+ * Select the arithmetic of fftbf_execute (enum fftbf_precision). The tensor-core forms
+ * compute the same quantity (Eq. fftbeamform, Eq. bf) with the zero-padded N-S transform
+ * as two GEMM stages on 16-bit operands with FP32 accumulation; they need pad_x = 4,
+ * pad_y = 512 and at most 256 N-S feeds (FFTBF_EUNSUPPORTED otherwise). With FP16
+ * operands the plan scales the E-W output so every intermediate stays finite and
+ * removes the scale from the result. Call before fftbf_execute; not thread-safe with it.
+ */
 int fftbf_plan_set_precision(fftbf_plan* plan, int precision);
 
 /*
@@ -149,6 +155,17 @@ const char* fftbf_last_error(void);
  * 2n values: re, im interleaved) with the decoder the kernels use.
  */
 int fftbf_debug_unpack(const uint8_t* in_dev, int64_t n, float* out_dev, void* stream);
+
+/*
+ * Test hook for the tensor-core building blocks: D[128][n] = A[128][32] B[n][32]^T with
+ * 16-bit operands (FP16, or BF16 if bf16 != 0), staged in the kernels' shared-memory
+ * layouts (A with the padded strides of the stage-2 operand if padded != 0), one pair of
+ * tcgen05.mma instructions, FP32 accumulation in tensor memory. n = 32, 64, 128 or 256.
+ * Device pointers, row-major. Synchronises `stream`; FFTBF_ETIMEOUT if the tensor core
+ * did not complete within one second.
+ */
+int fftbf_debug_tc_gemm(const uint16_t* a_dev, const uint16_t* b_dev, int n, int bf16,
+                        int padded, float* d_dev, void* stream);
 
 /*
  * fftbf_execute without a plan and without any device allocation. The paper has no

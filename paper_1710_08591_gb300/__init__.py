@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
-           "plan_sync", "destroy", "last_error", "debug_unpack", "execute_noalloc"]
+           "plan_sync", "destroy", "last_error", "debug_unpack", "execute_noalloc", "debug_tc_gemm"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
             L.fftbf_last_error.argtypes = []
             L.fftbf_execute_noalloc.restype = c_int
             L.fftbf_execute_noalloc.argtypes = [c_int] * 7 + [vp, vp, c_i64, vp, vp]
+            L.fftbf_debug_tc_gemm.restype = c_int
+            L.fftbf_debug_tc_gemm.argtypes = [vp, vp, c_int, c_int, c_int, vp, vp]
             L.fftbf_debug_unpack.restype = c_int
             L.fftbf_debug_unpack.argtypes = [vp, c_i64, vp, vp]
             _lib = L
@@ -218,6 +220,12 @@ def execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights, volts, T:
     memory); weights is a device tensor of nx*ny complex64 values or None."""
     _check(lib().fftbf_execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, _dptr(weights),
                                        _dptr(volts), int(T), _dptr(beams), _stream(stream)))
+
+
+def debug_tc_gemm(a, b, n: int, bf16: bool, padded: bool, d, stream=None) -> None:
+    """D[128][n] = A[128][32] B[n][32]^T on the tensor cores (test hook)."""
+    _check(lib().fftbf_debug_tc_gemm(_dptr(a), _dptr(b), int(n), int(bool(bf16)), int(bool(padded)),
+                                     _dptr(d), _stream(stream)))
 
 
 def debug_unpack(inp, n: int, out, stream=None) -> None:

@@ -1,0 +1,433 @@
+// Tensor-core form of the FFT-beam hot path for 4 E-W beams x 512 N-S beams over at most
+// 256 N-S feeds (the 4x256 lattice padded N-S to 2n, Eq. b2n-1).
+//
+// The zero-padded 512-point N-S transform of each (snapshot, E-W beam) is split as
+// 512 = 32 x 16 (n = n2 + 16 n1, k = k1 + 32 k2; inputs with n1 >= 16 are the padding):
+//   stage 1 (tcgen05.mma, M=128 N=64 K=32): rows (snapshot, E-W beam A, n2), the pruned
+//     32-point DFT X1[k1] = sum_{n1<16} x[n2 + 16 n1] W32^(n1 k1) as a real-embedded GEMM
+//     (complex values interleaved (re, im) along K and N);
+//   twiddle on the CUDA cores while draining TMEM: X1 *= W512^(n2 k1) in FP32, rounded
+//     to 16 bits and written transposed as the stage-2 operand;
+//   stage 2 (tcgen05.mma, M=128 N=32 K=32): rows (A, k1) of one snapshot, a 16-point DFT
+//     over n2 giving X[k1 + 32 k2]; warp A, lane k1 of the CTA read their own TMEM row,
+//     square it and add it to 16 register accumulators (Eq. bf), so integration over time
+//     and polarisation needs no cross-lane reduction.
+// Operands are FP16 or BF16 (the 4-bit inputs are exact in both), accumulation is FP32.
+// Unpacking, apodisation and the 4-point E-W DFT run in FP32 on the CUDA cores, as in the
+// FP32 form, and are rounded to 16 bits once (times a plan scale that keeps FP16 finite).
+// A CTA (4 warps, 128 TMEM columns) processes the two polarisations of one time sample
+// (two snapshots) per iteration; four CTAs share an SM's 512 TMEM columns. Every wait on
+// the tensor core is bounded by device time; on timeout the kernel records an error word
+// (FFTBF_ETIMEOUT at fftbf_plan_sync), frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "beam_fp32.cuh"
+#include "tc_ptx.cuh"
+
+namespace fftbf {
+
+namespace tcl {
+constexpr int NT = 128;
+constexpr int A1_LBO = 128, A1_SBO = 512, A1_BYTES = 16 * 512;     // 128 rows x K 32
+constexpr int A2_LBO = 144, A2_SBO = 592, A2_BYTES = 16 * 592;     // padded: conflict-free stores
+constexpr int B_LBO = 128, B_SBO = 512;
+constexpr int B1_BYTES = 8 * 512, B2_BYTES = 4 * 512;              // 64 and 32 rows x K 32
+constexpr uint32_t TMEM_COLS = 128;    // D1: cols 0-63, D2 (two snapshots): 64-95, 96-127
+constexpr uint64_t WAIT_NS = 1000000000ull;
+}  // namespace tcl
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (BF16) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+struct TcSmem {
+  int a1, a2, b1, b2, tw, w, raw, bars, taddr, total;
+};
+__host__ __device__ inline TcSmem tc_smem_layout(int nant) {
+  TcSmem L;
+  int o = 0;
+  auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
+  L.a1 = take(tcl::A1_BYTES);
+  L.a2 = take(2 * tcl::A2_BYTES);
+  L.b1 = take(tcl::B1_BYTES);
+  L.b2 = take(tcl::B2_BYTES);
+  L.tw = take(16 * 32 * 8);
+  L.w = take(nant * 8);
+  L.raw = take(2 * ((2 * nant + 15) & ~15));
+  L.bars = take(16);
+  L.taddr = take(16);
+  L.total = o;
+  return L;
+}
+
+// Copy a row-major [rows][32] 16-bit matrix into the canonical K-major layout.
+__device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* src, int rows,
+                                           int lbo, int sbo, int tid, int nt) {
+  for (int i = tid; i < rows * 16; i += nt) {         // pairs of 16-bit values
+    const int m = i >> 4, k = (i & 15) * 2;
+    const uint32_t v = (uint32_t)src[m * 32 + k] | ((uint32_t)src[m * 32 + k + 1] << 16);
+    *reinterpret_cast<uint32_t*>(dst + tc::kmajor_off(m, k, lbo, sbo)) = v;
+  }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
+  const BeamArgs& a = ta.b;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int nant = a.nx * a.ny;
+  const TcSmem L = tc_smem_layout(nant);
+  unsigned char* a1 = smem + L.a1;
+  unsigned char* a2 = smem + L.a2;
+  unsigned char* b1s = smem + L.b1;
+  unsigned char* b2s = smem + L.b2;
+  float2* twsm = reinterpret_cast<float2*>(smem + L.tw);     // [n2 16][k1 32] W512^(n2 k1)
+  float2* wsm = reinterpret_cast<float2*>(smem + L.w);
+  unsigned char* raw0 = smem + L.raw;
+  const int rawsz = (2 * nant + 15) & ~15;
+  uint64_t* bar1 = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* bar2 = bar1 + 1;
+  uint32_t* taddr_sm = reinterpret_cast<uint32_t*>(smem + L.taddr);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nitems = a.nwin * a.nfreq;
+  const int nsnap = a.n_int * a.npol;
+  const int niter = (nsnap + 1) / 2;
+
+  if ((int64_t)blockIdx.x >= nitems) return;
+
+  // ---- set-up: TMEM, barriers, constant operands, tables
+  if (warp == 0) {
+    tc::tmem_alloc(taddr_sm, tcl::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar1, 1);
+    tc::mbar_init(bar2, 1);
+    tc::mbar_init_fence();
+  }
+  load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
+  load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
+  for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 5) * (i & 31)];
+  for (int i = tid; i < nant; i += tcl::NT) wsm[i] = a.w[i];
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *taddr_sm;
+  const uint32_t tlane = (uint32_t)(32 * warp) << 16;        // this warp's TMEM lane quarter
+  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const uint32_t id1 = tc::idesc_f16(128, 64, BF16);
+  const uint32_t id2 = tc::idesc_f16(128, 32, BF16);
+  const float inv_s2 = 1.0f / (ta.scale * ta.scale);
+
+  auto stage = [&](int64_t itm, int it, unsigned char* raw) {
+    const int64_t jw = itm / a.nfreq;
+    const int f = (int)(itm - jw * a.nfreq);
+    if (vec16) {
+      const int cps = nant >> 4;
+      for (int q = tid; q < 2 * cps; q += tcl::NT) {
+        const int s = q / cps, g = 2 * it + s;
+        if (g < nsnap) {
+          const int64_t t = jw * a.n_int + g / a.npol;
+          const int p = g % a.npol;
+          const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + p) * (int64_t)nant;
+          cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
+        }
+      }
+    } else {
+      for (int q = tid; q < 2 * nant; q += tcl::NT) {
+        const int s = q / nant, g = 2 * it + s;
+        if (g < nsnap) {
+          const int64_t t = jw * a.n_int + g / a.npol;
+          const int p = g % a.npol;
+          raw[q] = a.volts[((t * a.nfreq + f) * a.npol + p) * (int64_t)nant + (q - s * nant)];
+        }
+      }
+    }
+  };
+
+  int64_t item = blockIdx.x;
+  int it = 0, cur = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  float acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+  stage(item, 0, raw0);
+  cp_async_commit();
+
+  while (true) {
+    int64_t nitem = item;
+    int nit = it + 1;
+    if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
+    const bool has_next = nitem < nitems;
+    cp_async_wait<0>();
+    __syncthreads();                                            // (S1)
+    if (has_next) stage(nitem, nit, raw0 + (cur ^ 1) * rawsz);
+    cp_async_commit();
+
+    // ---- unpack x weight, E-W DFT, scale, round: stage-1 operand A1[(s,A,n2)][(n1,c)]
+    const unsigned char* raw = raw0 + cur * rawsz;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = tid + q * tcl::NT;
+      const int s = c >> 8, iy = c & 255;
+      float2 z[4] = {czero(), czero(), czero(), czero()};
+      if (iy < a.nyf && 2 * it + s < nsnap) {
+        const unsigned char* rs = raw + s * nant;
+        if (a.ew_dft) {
+#pragma unroll
+          for (int ix = 0; ix < 4; ++ix)
+            z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+          Dft<4>::run(z);
+        } else {
+          for (int ix = 0; ix < a.nx; ++ix) {
+            const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+#pragma unroll
+            for (int A = 0; A < 4; ++A) z[A] = cadd(z[A], cmul(a.ex[A * a.nx + ix], col));
+          }
+        }
+      }
+#pragma unroll
+      for (int A = 0; A < 4; ++A) {
+        const int m = (s * 4 + A) * 16 + (iy & 15);
+        *reinterpret_cast<uint32_t*>(a1 + tc::kmajor_off(m, 2 * (iy >> 4), tcl::A1_LBO, tcl::A1_SBO)) =
+            pack2<BF16>(z[A].x * ta.scale, z[A].y * ta.scale);
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();                                            // (S2)
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(a1), sb = tc::smem_u32(b1s);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+        tc::mma_f16(tbase, tc::smem_desc(sa + kk * 2 * tcl::A1_LBO, tcl::A1_LBO, tcl::A1_SBO),
+                    tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id1, kk);
+      tc::mma_commit(bar1);
+    }
+    ok = tc::mbar_wait(bar1, phase, tcl::WAIT_NS);
+    if (!__syncthreads_and(ok)) break;
+    tc::fence_after_sync();
+
+    // ---- drain stage 1: twiddle W512^(n2 k1), round, store as A2[s][(A,k1)][(n2,c)]
+    {
+      const int m = 32 * warp + lane;
+      const int sA = m >> 4, n2 = m & 15, s = sA >> 2, A = sA & 3;
+      unsigned char* a2s = a2 + s * tcl::A2_BYTES;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t r[32];
+        tc::tmem_ld32(tbase + tlane + 32 * half, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k1 = 16 * half + j;
+          const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+          const float2 y = cmul(x, twsm[n2 * 32 + k1]);
+          *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
+              pack2<BF16>(y.x, y.y);
+        }
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();                                            // (S3)
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t sb = tc::smem_u32(b2s);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const uint32_t sa = tc::smem_u32(a2 + s * tcl::A2_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tbase + 64 + 32 * s,
+                      tc::smem_desc(sa + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
+                      tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id2, kk);
+      }
+      tc::mma_commit(bar2);
+    }
+    ok = tc::mbar_wait(bar2, phase, tcl::WAIT_NS);
+    if (!__syncthreads_and(ok)) break;
+    tc::fence_after_sync();
+
+    // ---- drain stage 2: warp A, lane k1 squares X[k1 + 32 k2] and accumulates
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      uint32_t r[32];
+      tc::tmem_ld32(tbase + tlane + 64 + 32 * s, r);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const float re = __uint_as_float(r[2 * k2]), im = __uint_as_float(r[2 * k2 + 1]);
+        acc[k2] = fmaf(re, re, fmaf(im, im, acc[k2]));
+      }
+    }
+    tc::fence_before_sync();
+    phase ^= 1u;
+
+    if (it == niter - 1) {
+      float* dst = a.beams + item * (int64_t)(4 * 512) + warp * 512 + lane;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        dst[32 * k2] = acc[k2] * inv_s2;
+        acc[k2] = 0.f;
+      }
+    }
+    if (!has_next) break;
+    item = nitem;
+    it = nit;
+    cur ^= 1;
+  }
+  if (!ok && tid == 0) atomicExch(ta.err, FFTBF_ETIMEOUT);
+  cp_async_wait<0>();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, tcl::TMEM_COLS);
+}
+
+bool tc_supported(int nx, int ny, int mx, int my) {
+  (void)nx;
+  return mx == 4 && my == 512 && (ny < my ? ny : my) <= 256 && nx * ny <= 16384;
+}
+
+int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
+  const BeamArgs& a = ta.b;
+  if (a.nwin <= 0) return FFTBF_OK;
+  const TcSmem L = tc_smem_layout(a.nx * a.ny);
+  // Each CTA holds 128 TMEM columns, so at most 4 may be resident on an SM: request
+  // enough shared memory that a fifth cannot fit (228 KB per SM, 1 KB reserved per CTA).
+  size_t smem = (size_t)L.total;
+  if (smem < 46 * 1024) smem = 46 * 1024;
+  if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
+  auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  FFTBF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tcl::NT, smem));
+  if (per_sm < 1) return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  if (per_sm > 4)
+    return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel: %d CTAs/SM would oversubscribe TMEM", per_sm);
+  const int64_t items = a.nwin * a.nfreq;
+  const int64_t grid = items < (int64_t)nsm * per_sm ? items : (int64_t)nsm * per_sm;
+  kern<<<(unsigned)grid, tcl::NT, smem, st>>>(ta);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+// ---------------------------------------------------------------- plan tables --
+// Real-embedded DFT matrices, transposed (row = output, column = input), interleaved
+// (re, im): B1t[2k1 + co][2n1 + ci] from W32^(n1 k1) for n1 < 16, k1 < 32 (the pruned
+// stage 1), B2t[2k2 + co][2n2 + ci] from W16^(n2 k2). FP64, rounded once to 16 bits.
+__global__ void tc_tables_kernel(uint16_t* b1, uint16_t* b2, int bf16) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  auto entry = [](int out_c, int in_c, double c, double sp) {
+    // X_re = x_re C - x_im S', X_im = x_re S' + x_im C with W = C + i S'
+    if (out_c == 0) return in_c == 0 ? c : -sp;
+    return in_c == 0 ? sp : c;
+  };
+  auto store = [&](uint16_t* dst, double v) {
+    if (bf16) {
+      __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      *dst = *reinterpret_cast<uint16_t*>(&h);
+    } else {
+      __half h = __float2half_rn((float)v);
+      *dst = *reinterpret_cast<uint16_t*>(&h);
+    }
+  };
+  if (i < 64 * 32) {
+    const int row = i >> 5, col = i & 31;
+    const int k1 = row >> 1, co = row & 1, n1 = col >> 1, ci = col & 1;
+    double s, c;
+    sincospi(2.0 * ((n1 * k1) % 32) / 32.0, &s, &c);
+    store(b1 + i, entry(co, ci, c, -s));
+  }
+  if (i < 32 * 32) {
+    const int row = i >> 5, col = i & 31;
+    const int k2 = row >> 1, co = row & 1, n2 = col >> 1, ci = col & 1;
+    double s, c;
+    sincospi(2.0 * ((n2 * k2) % 16) / 16.0, &s, &c);
+    store(b2 + i, entry(co, ci, c, -s));
+  }
+}
+
+int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st) {
+  tc_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, bf16 ? 1 : 0);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+// ------------------------------------------------------------ GEMM test hook --
+// D[128][n] = A[128][32] * B[n][32]^T with 16-bit operands (FP16 or BF16) in the
+// canonical layout (A's strides padded like the stage-2 operand if `padded`), one MMA
+// pair, FP32 in TMEM, read back with tcgen05.ld.
+template <bool BF16>
+__global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A, const uint16_t* B,
+                                                                int n, int padded, float* D, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int albo = padded ? tcl::A2_LBO : tcl::A1_LBO, asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
+  unsigned char* as = smem;
+  unsigned char* bs = smem + 16 * asbo;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(bs + (n / 8) * tcl::B_SBO);
+  uint32_t* taddr_sm = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(taddr_sm, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_init_fence();
+  }
+  load_kmajor(as, A, 128, albo, asbo, tid, 128);
+  load_kmajor(bs, B, n, tcl::B_LBO, tcl::B_SBO, tid, 128);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *taddr_sm;
+  if (tid == 0) {
+    const uint32_t id = tc::idesc_f16(128, n, BF16);
+    for (int kk = 0; kk < 2; ++kk)
+      tc::mma_f16(tbase, tc::smem_desc(tc::smem_u32(as) + kk * 2 * albo, albo, asbo),
+                  tc::smem_desc(tc::smem_u32(bs) + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO),
+                  id, kk);
+    tc::mma_commit(bar);
+  }
+  const bool ok = __syncthreads_and(tc::mbar_wait(bar, 0, tcl::WAIT_NS));
+  tc::fence_after_sync();
+  if (ok) {
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      uint32_t r[32];
+      tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + c0, r);
+      tc::tmem_wait_ld();
+      for (int j = 0; j < 32; ++j) D[(32 * warp + lane) * n + c0 + j] = __uint_as_float(r[j]);
+    }
+  } else if (tid == 0) {
+    atomicExch(err, FFTBF_ETIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 256);
+}
+
+int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
+                         float* D, int* err, cudaStream_t st) {
+  const int asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
+  const size_t smem = 16 * asbo + (n / 8) * tcl::B_SBO + 64;
+  auto kern = bf16 ? debug_tc_gemm_kernel<true> : debug_tc_gemm_kernel<false>;
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<1, 128, smem, st>>>(A, B, n, padded ? 1 : 0, D, err);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+}  // namespace fftbf

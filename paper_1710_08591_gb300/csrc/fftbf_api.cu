@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -88,13 +89,15 @@ fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, in
   if (e == cudaSuccess) e = cudaMalloc(&p->d_w, sizeof(float2) * nant);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_ex, sizeof(float2) * pad_x * nx);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, sizeof(float2) * pad_y);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e == cudaSuccess) {
-    if (weights) {
-      e = cudaMemcpy(p->d_w, weights, sizeof(float2) * nant, cudaMemcpyHostToDevice);
-    } else {
-      std::vector<float2> ones(nant, make_float2(1.f, 0.f));
-      e = cudaMemcpy(p->d_w, ones.data(), sizeof(float2) * nant, cudaMemcpyHostToDevice);
+    p->h_w.assign(2 * (size_t)nant, 0.f);
+    for (int i = 0; i < nant; ++i) {
+      p->h_w[2 * i] = weights ? weights[2 * i] : 1.f;
+      p->h_w[2 * i + 1] = weights ? weights[2 * i + 1] : 0.f;
     }
+    e = cudaMemcpy(p->d_w, p->h_w.data(), sizeof(float2) * nant, cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     cuda_error(e, "fftbf_plan_create");
@@ -116,9 +119,35 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
     p->precision = prec;
     return FFTBF_OK;
   }
-  if (prec == FFTBF_PREC_TC_FP16 || prec == FFTBF_PREC_TC_BF16)
-    return set_error(FFTBF_EUNSUPPORTED, "tensor-core form not available in this build");
-  return set_error(FFTBF_EINVAL, "unknown precision %d", prec);
+  if (prec != FFTBF_PREC_TC_FP16 && prec != FFTBF_PREC_TC_BF16)
+    return set_error(FFTBF_EINVAL, "unknown precision %d", prec);
+  if (!tc_supported(p->nx, p->ny, p->mx, p->my))
+    return set_error(FFTBF_EUNSUPPORTED,
+                     "tensor-core form needs pad_x = 4, pad_y = 512 and at most 256 N-S feeds "
+                     "(got nx=%d ny=%d pad_x=%d pad_y=%d)", p->nx, p->ny, p->mx, p->my);
+  DeviceGuard g(p->device);
+  if (!p->d_b1) {
+    FFTBF_CUDA_TRY(cudaMalloc(&p->d_b1, sizeof(uint16_t) * 64 * 32));
+    FFTBF_CUDA_TRY(cudaMalloc(&p->d_b2, sizeof(uint16_t) * 32 * 32));
+  }
+  const bool bf16 = prec == FFTBF_PREC_TC_BF16;
+  int rc = build_tc_tables(p->d_b1, p->d_b2, bf16, 0);
+  if (rc != FFTBF_OK) return rc;
+  FFTBF_CUDA_TRY(cudaDeviceSynchronize());
+  // FP16 range: |X1| <= 16 * max_iy sum_ix |w| * 8 sqrt(2); keep it below 30000.
+  double wmax = 0.0;
+  for (int iy = 0; iy < p->ny; ++iy) {
+    double sum = 0.0;
+    for (int ix = 0; ix < p->nx; ++ix) {
+      const double re = p->h_w[2 * ((size_t)ix * p->ny + iy)], im = p->h_w[2 * ((size_t)ix * p->ny + iy) + 1];
+      sum += std::sqrt(re * re + im * im);
+    }
+    wmax = std::max(wmax, sum);
+  }
+  const double bound = 16.0 * wmax * 8.0 * std::sqrt(2.0);
+  p->tc_scale = (!bf16 && bound > 30000.0) ? (float)(30000.0 / bound) : 1.f;
+  p->precision = prec;
+  return FFTBF_OK;
 }
 
 int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, void* stream) {
@@ -147,7 +176,19 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
   if (S > nsnap) S = nsnap;
   a.S = S;
   if (fp32_fft_supported(p->mx, p->my)) a.nst = radix_plan(p->my, &a.r0);
-  const int rc = launch_beams_fp32(a, p->nsm, st);
+  int rc;
+  if (p->precision == FFTBF_PREC_FP32) {
+    rc = launch_beams_fp32(a, p->nsm, st);
+  } else {
+    TcArgs ta{};
+    ta.b = a;
+    ta.b1 = p->d_b1;
+    ta.b2 = p->d_b2;
+    ta.scale = p->tc_scale;
+    ta.err = p->d_err;
+    ta.bf16 = p->precision == FFTBF_PREC_TC_BF16;
+    rc = launch_beams_tc(ta, p->nsm, st);
+  }
   if (rc == FFTBF_OK) remember_stream(p, st);
   return rc;
 }
@@ -174,6 +215,12 @@ int fftbf_plan_sync(fftbf_plan* p) {
   for (cudaStream_t st : p->streams_used) FFTBF_CUDA_TRY(cudaStreamSynchronize(st));
   if (p->pipe.copy) FFTBF_CUDA_TRY(cudaStreamSynchronize(p->pipe.copy));
   FFTBF_CUDA_TRY(cudaGetLastError());
+  int err = 0;
+  FFTBF_CUDA_TRY(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err != 0) {
+    FFTBF_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+    return set_error(err, "a device-side wait of the tensor-core kernel ran out");
+  }
   return FFTBF_OK;
 }
 
@@ -187,6 +234,9 @@ void fftbf_destroy(fftbf_plan* p) {
     cudaFree(p->d_w);
     cudaFree(p->d_ex);
     cudaFree(p->d_tw);
+    cudaFree(p->d_b1);
+    cudaFree(p->d_b2);
+    cudaFree(p->d_err);
   }
   delete p;
 }
@@ -195,6 +245,27 @@ int fftbf_debug_unpack(const uint8_t* in, int64_t n, float* out, void* stream) {
   if (n < 0) return set_error(FFTBF_EINVAL, "negative length");
   if (n > 0 && (!in || !out)) return set_error(FFTBF_EINVAL, "null pointer");
   return launch_debug_unpack(in, n, out, static_cast<cudaStream_t>(stream));
+}
+
+int fftbf_debug_tc_gemm(const uint16_t* a, const uint16_t* b, int n, int bf16, int padded,
+                        float* d, void* stream) {
+  if (!a || !b || !d) return set_error(FFTBF_EINVAL, "null pointer");
+  if (n != 32 && n != 64 && n != 128 && n != 256)
+    return set_error(FFTBF_EINVAL, "n must be 32, 64, 128 or 256");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* err = nullptr;
+  FFTBF_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  int rc = launch_debug_tc_gemm(a, b, n, bf16 != 0, padded != 0, d, err, st);
+  int h = 0;
+  if (rc == FFTBF_OK) {
+    cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_error(e, "debug tc gemm");
+    else if (h != 0) rc = set_error(h, "tensor-core wait ran out");
+  }
+  cudaFree(err);
+  return rc;
 }
 
 }  // extern "C"

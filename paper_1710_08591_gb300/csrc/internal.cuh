@@ -52,6 +52,21 @@ bool fp32_fft_supported(int mx, int my);
 bool fp32_n512_supported(const BeamArgs& a);
 int launch_beams_fp32_n512(const BeamArgs& a, int nsm, cudaStream_t st);
 int launch_debug_unpack(const uint8_t* in, int64_t n, float* out, cudaStream_t st);
+
+// Tensor-core form (4 E-W beams x 512 N-S beams over <= 256 N-S feeds).
+struct TcArgs {
+  BeamArgs b;
+  const uint16_t* b1;   // [64][32] stage-1 matrix (transposed, interleaved), FP16 or BF16 bits
+  const uint16_t* b2;   // [32][32] stage-2 DFT16 matrix
+  float scale;          // multiplies the E-W output before rounding to 16 bits
+  int* err;             // device error word (FFTBF_ETIMEOUT on a wait that ran out)
+  int bf16;
+};
+bool tc_supported(int nx, int ny, int mx, int my);
+int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st);
+int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st);
+int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
+                         float* D, int* err, cudaStream_t st);
 // FP64 table builders (device), rounded to FP32.
 int build_tables(int nx, int mx, int my, float2* ex, float2* tw, cudaStream_t st);
 
@@ -98,5 +113,10 @@ struct fftbf_plan {
   float2* d_tw = nullptr;
   fftbf::TiedTables tied;
   fftbf::HostPipe pipe;
+  std::vector<float> h_w;         // host copy of the weights (re, im interleaved)
+  uint16_t* d_b1 = nullptr;       // tensor-core stage matrices for the selected precision
+  uint16_t* d_b2 = nullptr;
+  float tc_scale = 1.f;
+  int* d_err = nullptr;           // device error word of bounded waits
   std::vector<cudaStream_t> streams_used;
 };
