@@ -438,6 +438,8 @@ int launch_fft_one(const BeamArgs& a, int nsm, cudaStream_t st) {
   const size_t smem = fft_smem_bytes(a);
   auto kern = beams_fp32_kernel<MX, LOG2N>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   FFTBF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
   if (per_sm < 1) return set_error(FFTBF_EUNSUPPORTED, "FP32 beam kernel does not fit on an SM");

@@ -205,6 +205,8 @@ static int launch_n512_mx(const BeamArgs& a, int nsm, cudaStream_t st) {
   const size_t smem = n512_smem_bytes(a, S, NW);
   auto kern = beams_fp32_n512_kernel<MX>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   FFTBF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem));
   if (per_sm < 1) return set_error(FFTBF_EUNSUPPORTED, "512-beam kernel does not fit on an SM");

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
   unsigned char* a2 = smem + L.a2;
   unsigned char* b1s = smem + L.b1;
   unsigned char* b2s = smem + L.b2;
-  float2* twsm = reinterpret_cast<float2*>(smem + L.tw);     // [n2 16][k1 32] W512^(n2 k1)
+  float2* twsm = reinterpret_cast<float2*>(smem + L.tw);     // [k1 32][n2 16] W512^(n2 k1)
   float2* wsm = reinterpret_cast<float2*>(smem + L.w);
   unsigned char* raw0 = smem + L.raw;
   const int rawsz = (2 * nant + 15) & ~15;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
   }
   load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
   load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
-  for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 5) * (i & 31)];
+  for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
   for (int i = tid; i < nant; i += tcl::NT) wsm[i] = a.w[i];
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
         for (int j = 0; j < 16; ++j) {
           const int k1 = 16 * half + j;
           const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-          const float2 y = cmul(x, twsm[n2 * 32 + k1]);
+          const float2 y = cmul(x, twsm[k1 * 16 + n2]);   // lanes: consecutive n2
           *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
               pack2<BF16>(y.x, y.y);
         }
@@ -311,11 +311,21 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
   auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  FFTBF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tcl::NT, smem));
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+  // Residency from registers and shared memory (the occupancy query is conservative for
+  // kernels that allocate tensor memory); never more than 4 CTAs of 128 TMEM columns.
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  FFTBF_CUDA_TRY(cudaGetDevice(&dev));
+  FFTBF_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  FFTBF_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  cudaFuncAttributes fa{};
+  FFTBF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  const int by_smem = smem_sm / (int)(smem + 1024);
+  const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * tcl::NT);
+  int per_sm = by_smem < by_regs ? by_smem : by_regs;
+  if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
-  if (per_sm > 4)
-    return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel: %d CTAs/SM would oversubscribe TMEM", per_sm);
   const int64_t items = a.nwin * a.nfreq;
   const int64_t grid = items < (int64_t)nsm * per_sm ? items : (int64_t)nsm * per_sm;
   kern<<<(unsigned)grid, tcl::NT, smem, st>>>(ta);
