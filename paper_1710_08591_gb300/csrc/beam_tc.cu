@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "beam_fp32.cuh"
 #include "tc_ptx.cuh"
 
@@ -82,7 +84,8 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 template <bool BF16>
 __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* smem = smem_tc;
   const int nant = a.nx * a.ny;
   const TcSmem L = tc_smem_layout(nant);
   unsigned char* a1 = smem + L.a1;
@@ -295,40 +298,375 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
   if (warp == 0) tc::tmem_dealloc(tbase, tcl::TMEM_COLS);
 }
 
+// ------------------------------------------------------------------------------------
+// Warp-specialised, double-buffered version of the same computation. Roles per CTA:
+//   warps 0-3  producers: stage bytes (cp.async), unpack x weight, E-W DFT, round -> A1[b]
+//   warps 4-7  drainers:  D1[b] -> twiddle -> A2[b]; D2[b] -> |.|^2 -> accumulators
+//   warp 8     issuer:    one lane issues MMA1(p) and MMA2(p-1) and commits them
+// for snapshot pairs p = 0, 1, ... with buffers b = p mod 2. Hand-offs are mbarriers:
+//   a1_full[b]  producers -> issuer      d1_full[b]  issuer (commit) -> drainers, producers
+//   d1_empty[b] drainers -> issuer       a2_full[b]  drainers -> issuer
+//   d2_full[b]  issuer (commit) -> drainers   d2_empty[b] drainers -> issuer
+// so the unpacking of pair p+1, the tensor-core stages and the draining of pair p overlap.
+// Two CTAs per SM (256 TMEM columns each: D1[2] x 64, D2[2] x 64).
+namespace tcp {
+constexpr int NT = 288;
+constexpr uint32_t TMEM_COLS = 256;
+enum { A1F = 0, D1F = 2, D1E = 4, A2F = 6, D2F = 8, D2E = 10, NBAR = 12 };
+}  // namespace tcp
+
+struct TcPipeSmem {
+  int a1, a2, b1, b2, tw, w, lut, raw, bars, misc, total;
+};
+__host__ __device__ inline TcPipeSmem tcp_smem_layout(int nant) {
+  TcPipeSmem L;
+  int o = 0;
+  auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
+  L.a1 = take(2 * tcl::A1_BYTES);
+  L.a2 = take(4 * tcl::A2_BYTES);
+  L.b1 = take(tcl::B1_BYTES);
+  L.b2 = take(tcl::B2_BYTES);
+  L.tw = take(16 * 32 * 8);
+  L.w = take(nant * 8);
+  L.lut = take(256 * 8);
+  L.raw = take(2 * ((2 * nant + 15) & ~15));
+  L.bars = take(tcp::NBAR * 8);
+  L.misc = take(16);
+  L.total = o;
+  return L;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs ta) {
+  const BeamArgs& a = ta.b;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* smem = smem_tc;
+  const int nant = a.nx * a.ny;
+  const TcPipeSmem L = tcp_smem_layout(nant);
+  unsigned char* a1 = smem + L.a1;
+  unsigned char* a2 = smem + L.a2;
+  unsigned char* b1s = smem + L.b1;
+  unsigned char* b2s = smem + L.b2;
+  float2* twsm = reinterpret_cast<float2*>(smem + L.tw);   // [k1 32][n2 16]
+  float2* wsm = reinterpret_cast<float2*>(smem + L.w);
+  float2* lut = reinterpret_cast<float2*>(smem + L.lut);   // byte -> (re, im)
+  unsigned char* raw0 = smem + L.raw;
+  const int rawsz = (2 * nant + 15) & ~15;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint32_t* taddr_sm = reinterpret_cast<uint32_t*>(smem + L.misc);
+  volatile int* abort_sm = reinterpret_cast<volatile int*>(smem + L.misc + 4);
+  volatile int* pvote = reinterpret_cast<volatile int*>(smem + L.misc + 8);    // producers
+  volatile int* evote = reinterpret_cast<volatile int*>(smem + L.misc + 12);   // drainers
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nitems = a.nwin * a.nfreq;
+  const int nsnap = a.n_int * a.npol;
+  const int niter = (nsnap + 1) / 2;
+  if ((int64_t)blockIdx.x >= nitems) return;
+  const int64_t my_items = (nitems - 1 - blockIdx.x) / gridDim.x + 1;
+  const int64_t P = my_items * niter;                 // snapshot pairs of this CTA
+
+  if (warp == 8) {
+    tc::tmem_alloc(taddr_sm, tcp::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    const uint32_t counts[tcp::NBAR] = {128, 128, 1, 1, 128, 128, 128, 128, 1, 1, 128, 128};
+    for (int i = 0; i < tcp::NBAR; ++i) tc::mbar_init(bars + i, counts[i]);
+    tc::mbar_init_fence();
+    *abort_sm = 0;
+  }
+  load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcp::NT);
+  load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcp::NT);
+  for (int i = tid; i < 512; i += tcp::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
+  for (int i = tid; i < nant; i += tcp::NT) wsm[i] = a.w[i];
+  for (int i = tid; i < 256; i += tcp::NT) lut[i] = unpack_byte((unsigned)i);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *taddr_sm;
+  const uint64_t W = tcl::WAIT_NS;
+  auto fail = [&]() { *abort_sm = 1; atomicExch(ta.err, FFTBF_ETIMEOUT); };
+
+  if (warp < 4) {
+    // ================================================================ producers
+    const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+    const bool scaled = ta.scale != 1.f;
+    auto stage = [&](int64_t itm, int it, unsigned char* raw) {
+      const int64_t jw = itm / a.nfreq;
+      const int f = (int)(itm - jw * a.nfreq);
+      if (vec16) {
+        const int cps = nant >> 4;
+        for (int q = tid; q < 2 * cps; q += 128) {
+          const int s = q / cps, g = 2 * it + s;
+          if (g < nsnap) {
+            const int64_t t = jw * a.n_int + g / a.npol;
+            const int pp = g % a.npol;
+            const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + pp) * (int64_t)nant;
+            cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
+          }
+        }
+      } else {
+        for (int q = tid; q < 2 * nant; q += 128) {
+          const int s = q / nant, g = 2 * it + s;
+          if (g < nsnap) {
+            const int64_t t = jw * a.n_int + g / a.npol;
+            const int pp = g % a.npol;
+            raw[q] = a.volts[((t * a.nfreq + f) * a.npol + pp) * (int64_t)nant + (q - s * nant)];
+          }
+        }
+      }
+    };
+    int64_t item = blockIdx.x;
+    int it = 0;
+    stage(item, 0, raw0);
+    cp_async_commit();
+    for (int64_t p = 0; p < P; ++p) {
+      int64_t nitem = item;
+      int nit = it + 1;
+      if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
+      tc::named_sync(1, 128);                         // phase B of p-1 done: raw[(p+1)&1] free
+      if (p + 1 < P) stage(nitem, nit, raw0 + ((p + 1) & 1) * rawsz);
+      cp_async_commit();
+      cp_async_wait<1>();
+      const int b = (int)(p & 1);
+      const uint32_t u = (uint32_t)(p >> 1);
+      if (tid == 0) *pvote = (u == 0) || tc::mbar_wait_abortable(bars + tcp::D1F + b, (u - 1) & 1, W, abort_sm);
+      tc::named_sync(1, 128);                         // bytes of p visible; A1[b] free (or abort)
+      if (!*pvote) { if (tid == 0) fail(); break; }
+      const unsigned char* raw = raw0 + (p & 1) * rawsz;
+      unsigned char* a1b = a1 + b * tcl::A1_BYTES;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = tid + q * 128;
+        const int s = c >> 8, iy = c & 255;
+        float2 z[4] = {czero(), czero(), czero(), czero()};
+        if (iy < a.nyf && 2 * it + s < nsnap) {
+          const unsigned char* rs = raw + s * nant;
+          if (a.ew_dft) {
+#pragma unroll
+            for (int ix = 0; ix < 4; ++ix) z[ix] = cmul(wsm[ix * a.ny + iy], lut[rs[ix * a.ny + iy]]);
+            Dft<4>::run(z);
+          } else {
+            for (int ix = 0; ix < a.nx; ++ix) {
+              const float2 col = cmul(wsm[ix * a.ny + iy], lut[rs[ix * a.ny + iy]]);
+#pragma unroll
+              for (int A = 0; A < 4; ++A) z[A] = cadd(z[A], cmul(a.ex[A * a.nx + ix], col));
+            }
+          }
+          if (scaled) {
+#pragma unroll
+            for (int A = 0; A < 4; ++A) z[A] = make_float2(z[A].x * ta.scale, z[A].y * ta.scale);
+          }
+        }
+#pragma unroll
+        for (int A = 0; A < 4; ++A) {
+          const int m = (s * 4 + A) * 16 + (iy & 15);
+          *reinterpret_cast<uint32_t*>(a1b + tc::kmajor_off(m, 2 * (iy >> 4), tcl::A1_LBO, tcl::A1_SBO)) =
+              pack2<BF16>(z[A].x, z[A].y);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      tc::mbar_arrive(bars + tcp::A1F + b);
+      item = nitem;
+      it = nit;
+    }
+    cp_async_wait<0>();
+  } else if (warp < 8) {
+    // ================================================================= drainers
+    const int q4 = warp - 4;                         // TMEM lane quarter
+    const uint32_t tlane = (uint32_t)(32 * q4) << 16;
+    const int etid = tid - 128;
+    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
+    float acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+    int64_t qitem = blockIdx.x;                      // item of the pair being accumulated
+    int qit = 0;
+    for (int64_t p = 0; p <= P; ++p) {
+      if (p < P) {
+        const int b = (int)(p & 1);
+        const uint32_t u = (uint32_t)(p >> 1);
+        if (etid == 0) *evote = tc::mbar_wait_abortable(bars + tcp::D1F + b, u & 1, W, abort_sm);
+        tc::named_sync(2, 128);
+        if (!*evote) { if (etid == 0) fail(); break; }
+        tc::fence_after_sync();
+        const int m = 32 * q4 + lane;
+        const int sA = m >> 4, n2 = m & 15, s = sA >> 2, A = sA & 3;
+        unsigned char* a2s = a2 + (2 * b + s) * tcl::A2_BYTES;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t r[32];
+          tc::tmem_ld32(tbase + tlane + 64 * b + 32 * half, r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int k1 = 16 * half + j;
+            const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            const float2 y = cmul(x, twsm[k1 * 16 + n2]);
+            *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
+                pack2<BF16>(y.x, y.y);
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(bars + tcp::D1E + b);
+        tc::fence_proxy_async_smem();
+        tc::mbar_arrive(bars + tcp::A2F + b);
+      }
+      if (p >= 1) {
+        const int64_t q = p - 1;
+        const int b = (int)(q & 1);
+        const uint32_t u = (uint32_t)(q >> 1);
+        if (etid == 0) *evote = tc::mbar_wait_abortable(bars + tcp::D2F + b, u & 1, W, abort_sm);
+        tc::named_sync(2, 128);
+        if (!*evote) { if (etid == 0) fail(); break; }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          uint32_t r[32];
+          tc::tmem_ld32(tbase + tlane + 128 + 64 * b + 32 * s, r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const float re = __uint_as_float(r[2 * k2]), im = __uint_as_float(r[2 * k2 + 1]);
+            acc[k2] = fmaf(re, re, fmaf(im, im, acc[k2]));
+          }
+        }
+        tc::fence_before_sync();
+        tc::mbar_arrive(bars + tcp::D2E + b);
+        if (qit == niter - 1) {
+          float* dst = a.beams + qitem * (int64_t)(4 * 512) + q4 * 512 + lane;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            dst[32 * k2] = acc[k2] * inv_s2;
+            acc[k2] = 0.f;
+          }
+          qitem += gridDim.x;
+          qit = 0;
+        } else {
+          ++qit;
+        }
+      }
+    }
+  } else if (lane == 0) {
+    // =================================================================== issuer
+    const uint32_t id1 = tc::idesc_f16(128, 64, BF16);
+    const uint32_t id2 = tc::idesc_f16(128, 32, BF16);
+    const uint32_t sb1 = tc::smem_u32(b1s), sb2 = tc::smem_u32(b2s);
+    for (int64_t p = 0; p <= P; ++p) {
+      if (p < P) {
+        const int b = (int)(p & 1);
+        const uint32_t u = (uint32_t)(p >> 1);
+        if (!tc::mbar_wait_abortable(bars + tcp::A1F + b, u & 1, W, abort_sm) ||
+            (u >= 1 && !tc::mbar_wait_abortable(bars + tcp::D1E + b, (u - 1) & 1, W, abort_sm))) {
+          fail();
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(a1 + b * tcl::A1_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tbase + 64 * b, tc::smem_desc(sa + kk * 2 * tcl::A1_LBO, tcl::A1_LBO, tcl::A1_SBO),
+                      tc::smem_desc(sb1 + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id1, kk);
+        tc::mma_commit(bars + tcp::D1F + b);
+      }
+      if (p >= 1) {
+        const int64_t q = p - 1;
+        const int b = (int)(q & 1);
+        const uint32_t u = (uint32_t)(q >> 1);
+        if (!tc::mbar_wait_abortable(bars + tcp::A2F + b, u & 1, W, abort_sm) ||
+            (u >= 1 && !tc::mbar_wait_abortable(bars + tcp::D2E + b, (u - 1) & 1, W, abort_sm))) {
+          fail();
+          break;
+        }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const uint32_t sa = tc::smem_u32(a2 + (2 * b + s) * tcl::A2_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tbase + 128 + 64 * b + 32 * s,
+                        tc::smem_desc(sa + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
+                        tc::smem_desc(sb2 + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id2, kk);
+        }
+        tc::mma_commit(bars + tcp::D2F + b);
+      }
+    }
+  }
+  __syncwarp();
+  // Every role has left its loop. The tensor core may still be finishing the last
+  // commits; wait (bounded) for the final stage-2 commit before freeing TMEM.
+  if (tid == 0 && P > 0 && !*abort_sm) {
+    const int64_t q = P - 1;
+    tc::mbar_wait(bars + tcp::D2F + (int)(q & 1), (uint32_t)((q >> 1) & 1), W);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 8) tc::tmem_dealloc(tbase, tcp::TMEM_COLS);
+}
+
 bool tc_supported(int nx, int ny, int mx, int my) {
   (void)nx;
   return mx == 4 && my == 512 && (ny < my ? ny : my) <= 256 && nx * ny <= 16384;
 }
 
-int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
-  const BeamArgs& a = ta.b;
-  if (a.nwin <= 0) return FFTBF_OK;
-  const TcSmem L = tc_smem_layout(a.nx * a.ny);
-  // Each CTA holds 128 TMEM columns, so at most 4 may be resident on an SM: request
-  // enough shared memory that a fifth cannot fit (228 KB per SM, 1 KB reserved per CTA).
-  size_t smem = (size_t)L.total;
-  if (smem < 46 * 1024) smem = 46 * 1024;
-  if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
-  auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
-  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      cudaSharedmemCarveoutMaxShared));
+static int tc_residency(const void* kern, size_t smem, int nthreads, int max_ctas, int* per_sm) {
   // Residency from registers and shared memory (the occupancy query is conservative for
-  // kernels that allocate tensor memory); never more than 4 CTAs of 128 TMEM columns.
+  // kernels that allocate tensor memory), capped by the TMEM budget.
   int dev = 0, smem_sm = 0, regs_sm = 0;
   FFTBF_CUDA_TRY(cudaGetDevice(&dev));
   FFTBF_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   FFTBF_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
   cudaFuncAttributes fa{};
   FFTBF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  const int warps = (nthreads + 31) / 32;
   const int by_smem = smem_sm / (int)(smem + 1024);
-  const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * tcl::NT);
-  int per_sm = by_smem < by_regs ? by_smem : by_regs;
-  if (per_sm > 4) per_sm = 4;
-  if (per_sm < 1) return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * 32 * warps);
+  int n = by_smem < by_regs ? by_smem : by_regs;
+  if (n > max_ctas) n = max_ctas;
+  *per_sm = n;
+  if (n < 1) return set_error(FFTBF_EUNSUPPORTED, "tensor-core kernel does not fit on an SM");
+  return FFTBF_OK;
+}
+
+int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
+  const BeamArgs& a = ta.b;
+  if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
+  const char* simple = getenv("FFTBF_TC_SIMPLE");
+  if (simple && simple[0] && simple[0] != '0') {
+    const TcSmem L = tc_smem_layout(a.nx * a.ny);
+    // at most 4 CTAs of 128 TMEM columns per SM: keep a fifth from fitting
+    size_t smem = (size_t)L.total;
+    if (smem < 46 * 1024) smem = 46 * 1024;
+    if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
+    auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
+    FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        cudaSharedmemCarveoutMaxShared));
+    int per_sm = 0;
+    int rc = tc_residency((const void*)kern, smem, tcl::NT, 4, &per_sm);
+    if (rc != FFTBF_OK) return rc;
+    const int64_t grid = items < (int64_t)nsm * per_sm ? items : (int64_t)nsm * per_sm;
+    kern<<<(unsigned)grid, tcl::NT, smem, st>>>(ta);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+    return FFTBF_OK;
+  }
+  const TcPipeSmem L = tcp_smem_layout(a.nx * a.ny);
+  // at most 2 CTAs of 256 TMEM columns per SM: keep a third from fitting
+  size_t smem = (size_t)L.total;
+  if (smem < 77 * 1024) smem = 77 * 1024;
+  if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
+  auto kern = ta.bf16 ? beams_tc_pipe_kernel<true> : beams_tc_pipe_kernel<false>;
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+  int per_sm = 0;
+  int rc = tc_residency((const void*)kern, smem, tcp::NT, 2, &per_sm);
+  if (rc != FFTBF_OK) return rc;
   const int64_t grid = items < (int64_t)nsm * per_sm ? items : (int64_t)nsm * per_sm;
-  kern<<<(unsigned)grid, tcl::NT, smem, st>>>(ta);
+  kern<<<(unsigned)grid, tcp::NT, smem, st>>>(ta);
   FFTBF_CUDA_TRY(cudaGetLastError());
   return FFTBF_OK;
 }
@@ -382,7 +720,8 @@ int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st) {
 template <bool BF16>
 __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A, const uint16_t* B,
                                                                 int n, int padded, float* D, int* err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* smem = smem_tc;
   const int albo = padded ? tcl::A2_LBO : tcl::A1_LBO, asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
   unsigned char* as = smem;
   unsigned char* bs = smem + 16 * asbo;
