@@ -634,8 +634,10 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const BeamArgs& a = ta.b;
   if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
-  const char* simple = getenv("FFTBF_TC_SIMPLE");
-  if (simple && simple[0] && simple[0] != '0') {
+  // The serial kernel (four CTAs per SM, every warp in every phase) measures faster than
+  // the warp-specialised pipeline on the 4x256 lattice; FFTBF_TC_PIPE=1 selects the latter.
+  const char* pipe = getenv("FFTBF_TC_PIPE");
+  if (!(pipe && pipe[0] && pipe[0] != '0')) {
     const TcSmem L = tc_smem_layout(a.nx * a.ny);
     // at most 4 CTAs of 128 TMEM columns per SM: keep a fifth from fitting
     size_t smem = (size_t)L.total;

@@ -82,13 +82,13 @@ def test_tc_beams_match_oracle(form, shape, wk):
 
 @pytest.mark.parametrize("form", ["fp16", "bf16"])
 def test_tc_serial_kernel_matches_pipelined(form, monkeypatch):
-    """The one-role-per-CTA kernel (FFTBF_TC_SIMPLE=1) and the warp-specialised pipelined
-    kernel compute the same sums in the same order: bit-identical results."""
+    """The serial kernel (default) and the warp-specialised pipelined kernel
+    (FFTBF_TC_PIPE=1) compute the same sums in the same order: bit-identical results."""
     shape = (4, 256, 4, 512, 2, 3, 96, 48)
     v, w = make_case(*shape, weights="half_sine", seed=8)
-    piped = run_tc(v, w, shape, form)
-    monkeypatch.setenv("FFTBF_TC_SIMPLE", "1")
     serial = run_tc(v, w, shape, form)
+    monkeypatch.setenv("FFTBF_TC_PIPE", "1")
+    piped = run_tc(v, w, shape, form)
     assert np.array_equal(piped, serial)
 
 
