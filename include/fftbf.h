@@ -140,6 +140,33 @@ int fftbf_execute_host(fftbf_plan* plan, const uint8_t* volts_host, int64_t T,
                        float* beams_host, int n_tied, const double* u, const double* v,
                        float* tied_host, void* stream);
 
+/*
+ * Batches: several plans (arrays of different lattice sizes, channel counts and weights)
+ * transformed by ONE persistent launch of the FP32 form. Work items are (array, window,
+ * channel) taken from a device work queue, costliest arrays first; each array runs the
+ * transform of its own shape, with a snapshots-per-step tile picked for it by timing the
+ * candidates on the device at creation. Supported shapes (pad_x x pad_y, pad_y >= ny):
+ * 4x512, 8x128, 16x32, 2x1024, 1x2048, 3x256 (the N-S axis padded to twice the next
+ * power of two of 256, 64, 16, 512, 1024, 128 feeds); others give FFTBF_EUNSUPPORTED.
+ * The plans must outlive the batch, be on one device and not change precision.
+ */
+typedef struct fftbf_batch fftbf_batch;
+/* n plans (1..64); allocates the work table and runs the autotuner. NULL on error. */
+fftbf_batch* fftbf_batch_create(fftbf_plan* const* plans, int n);
+/*
+ * One pass of every plan over T samples (T a multiple of every plan's n_int):
+ * volts_dev[i] / beams_dev[i] are host arrays of n device pointers laid out as in
+ * fftbf_execute for plan i. Each array's beams are bit-identical to a batch of that
+ * array alone in the same process (the autotuner's choice is kept per lattice shape). On a non-default stream the launch is captured in a CUDA graph and
+ * replayed while stream, T and the pointers stay the same.
+ */
+int fftbf_batch_execute(fftbf_batch* batch, const uint8_t* const* volts_dev, int64_t T,
+                        float* const* beams_dev, void* stream);
+/* Snapshots per step the autotuner chose for plan i of the batch (>= 1), or < 0. */
+int fftbf_batch_tuned_steps(const fftbf_batch* batch, int i);
+/* Free the batch (waits for its last launch). NULL is a no-op. */
+void fftbf_batch_destroy(fftbf_batch* batch);
+
 /* Wait for all work the plan has enqueued; returns the first device-side error seen
  * (e.g. FFTBF_ETIMEOUT) and clears it. */
 int fftbf_plan_sync(fftbf_plan* plan);
@@ -149,6 +176,8 @@ void fftbf_destroy(fftbf_plan* plan);
 
 /* Message of the last error on the calling thread ("" if none). Owned by the library. */
 const char* fftbf_last_error(void);
+/* Status code of that error (FFTBF_OK if none): the code behind a NULL from a constructor. */
+int fftbf_last_error_code(void);
 
 /*
  * Test hook for the bit layout: decode n bytes at in_dev into out_dev (device float,

@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
-           "plan_sync", "destroy", "last_error", "debug_unpack", "execute_noalloc", "debug_tc_gemm"]
+           "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "Batch", "batch_create",
+           "batch_execute", "batch_tuned_steps", "batch_destroy"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
@@ -71,8 +72,18 @@ def lib() -> ctypes.CDLL:
             L.fftbf_destroy.argtypes = [vp]
             L.fftbf_last_error.restype = ctypes.c_char_p
             L.fftbf_last_error.argtypes = []
+            L.fftbf_last_error_code.restype = c_int
+            L.fftbf_last_error_code.argtypes = []
             L.fftbf_execute_noalloc.restype = c_int
             L.fftbf_execute_noalloc.argtypes = [c_int] * 7 + [vp, vp, c_i64, vp, vp]
+            L.fftbf_batch_create.restype = vp
+            L.fftbf_batch_create.argtypes = [vp, c_int]
+            L.fftbf_batch_execute.restype = c_int
+            L.fftbf_batch_execute.argtypes = [vp, vp, c_i64, vp, vp]
+            L.fftbf_batch_tuned_steps.restype = c_int
+            L.fftbf_batch_tuned_steps.argtypes = [vp, c_int]
+            L.fftbf_batch_destroy.restype = None
+            L.fftbf_batch_destroy.argtypes = [vp]
             L.fftbf_debug_tc_gemm.restype = c_int
             L.fftbf_debug_tc_gemm.argtypes = [vp, vp, c_int, c_int, c_int, vp, vp]
             L.fftbf_debug_unpack.restype = c_int
@@ -83,6 +94,10 @@ def lib() -> ctypes.CDLL:
 
 def last_error() -> str:
     return lib().fftbf_last_error().decode()
+
+
+def last_error_code() -> int:
+    return int(lib().fftbf_last_error_code())
 
 
 def _check(rc: int) -> int:
@@ -142,7 +157,7 @@ class Plan:
         h = lib().fftbf_plan_create(nx, ny, pad_x, pad_y, npol, nfreq, n_int,
                                     None if w is None else w.ctypes.data)
         if not h:
-            raise FftbfError(-1, last_error())
+            raise FftbfError(last_error_code(), last_error())
         self.handle = h
 
     def __getattr__(self, k):
@@ -204,6 +219,61 @@ def execute_host(plan: Plan, volts: np.ndarray, T: int, beams: np.ndarray, n_tie
         plan.handle, volts.ctypes.data, int(T), beams.ctypes.data, int(n_tied),
         None if uu is None else uu.ctypes.data, None if vv is None else vv.ctypes.data,
         None if tied is None else tied.ctypes.data, _stream(stream)))
+
+
+class Batch:
+    """Owning handle of an ``fftbf_batch`` over a list of plans (kept alive here)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = lib().fftbf_batch_create(arr, len(self.plans))
+        if not h:
+            raise FftbfError(last_error_code(), last_error())
+        self.handle = h
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            lib().fftbf_batch_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_create(plans) -> Batch:
+    return Batch(plans)
+
+
+def batch_execute(batch: Batch, volts, T: int, beams, stream=None) -> None:
+    """One persistent launch over all plans of the batch; volts/beams: sequences of device
+    buffers, one per plan."""
+    n = len(batch.plans)
+    if len(volts) != n or len(beams) != n:
+        raise ValueError(f"need {n} voltage and beam buffers")
+    va = (ctypes.c_void_p * n)(*[_dptr(v) for v in volts])
+    ba = (ctypes.c_void_p * n)(*[_dptr(b) for b in beams])
+    _check(lib().fftbf_batch_execute(batch.handle, va, int(T), ba, _stream(stream)))
+
+
+def batch_tuned_steps(batch: Batch, i: int) -> int:
+    r = lib().fftbf_batch_tuned_steps(batch.handle, i)
+    if r < 0:
+        raise FftbfError(r, last_error())
+    return r
+
+
+def batch_destroy(batch: Batch) -> None:
+    batch.close()
 
 
 def plan_sync(plan: Plan) -> None:

@@ -14,6 +14,7 @@
 namespace fftbf {
 
 static thread_local std::string g_error;
+static thread_local int g_error_code = FFTBF_OK;
 
 int set_error(int code, const char* fmt, ...) {
   char buf[512];
@@ -22,6 +23,7 @@ int set_error(int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_error = buf;
+  g_error_code = code;
   return code;
 }
 
@@ -64,6 +66,7 @@ using namespace fftbf;
 extern "C" {
 
 const char* fftbf_last_error(void) { return g_error.c_str(); }
+int fftbf_last_error_code(void) { return g_error_code; }
 
 fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, int nfreq,
                               int n_int, const float* weights) {

@@ -1,0 +1,78 @@
+"""Batched uneven lattices in one persistent launch: parity with the oracle per array,
+bit-identical results alone and in the mix, graph replay, autotuned tiles."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import TOL_BEAM, make_case, oracle_beams
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1710_08591_gb300 as fb  # noqa: E402
+
+# (nx, ny): N-S padded to twice the next power of two, E-W unpadded
+LATTICES = synth.BATCH_LATTICES
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fb.build()
+    fb.lib()
+
+
+def _arrays(nfreqs, T, n_int, npol=2, seed=40):
+    arrs = []
+    for k, ((nx, ny), nf) in enumerate(zip(LATTICES, nfreqs)):
+        mx, my = nx, 2 * synth.next_pow2(ny)
+        v, w = make_case(nx, ny, mx, my, npol, nf, T, n_int,
+                         weights="half_sine" if k % 2 == 0 else "random", seed=seed + k)
+        arrs.append(dict(shape=(nx, ny, mx, my, npol, nf, n_int), v=v, w=w))
+    return arrs
+
+
+def _run(arrs, T, stream=None, repeat=1):
+    plans = [fb.plan_create(*a["shape"], weights=a["w"]) for a in arrs]
+    dvs = [torch.from_numpy(a["v"].reshape(-1)).cuda() for a in arrs]
+    outs = [torch.full((T // a["shape"][6], a["shape"][5], a["shape"][2], a["shape"][3]),
+                       float("nan"), device="cuda") for a in arrs]
+    with fb.batch_create(plans) as b:
+        steps = [fb.batch_tuned_steps(b, i) for i in range(len(plans))]
+        for _ in range(repeat):
+            fb.batch_execute(b, dvs, T, outs, stream)
+        torch.cuda.synchronize()
+    res = [o.cpu().numpy() for o in outs]
+    for p in plans:
+        p.close()
+    return res, steps
+
+
+def test_batch_matches_oracle_every_array():
+    T, n_int = 32, 16
+    arrs = _arrays([3, 2, 4, 2, 2, 3], T, n_int)
+    got, steps = _run(arrs, T)
+    assert all(s >= 1 for s in steps)
+    for a, g in zip(arrs, got):
+        nx, ny, mx, my, npol, nf, n_int_ = a["shape"]
+        ref = oracle_beams(a["v"], a["w"], nx, ny, mx, my, npol, nf, n_int_)
+        err = np.abs(g - ref) / ref
+        assert err.max() <= TOL_BEAM, (a["shape"], err.max())
+
+
+def test_batch_bit_identical_alone_and_in_mix_and_replayed():
+    T, n_int = 64, 32
+    arrs = _arrays([2, 3, 2, 2, 1, 2], T, n_int, seed=50)
+    s = torch.cuda.Stream()
+    mix, _ = _run(arrs, T, stream=s, repeat=3)          # captured once, replayed
+    for k in (0, 4, 5):
+        alone, _ = _run([arrs[k]], T, stream=s)
+        assert np.array_equal(alone[0], mix[k])
+
+
+def test_batch_rejects_unsupported_shape():
+    with fb.plan_create(5, 12, 5, 24, 1, 2, 4) as p:
+        with pytest.raises(fb.FftbfError) as e:
+            fb.batch_create([p])
+        assert e.value.code == -5
