@@ -167,6 +167,41 @@ int fftbf_batch_tuned_steps(const fftbf_batch* batch, int i);
 /* Free the batch (waits for its last launch). NULL is a no-op. */
 void fftbf_batch_destroy(fftbf_batch* batch);
 
+/*
+ * Continuous-batching server for voltage frames from many independent streams. A frame is
+ * one window (n_int samples) of one lattice plan: host uint8 [n_int][nfreq][npol][nx][ny];
+ * its result is that window's beams, host float [nfreq][pad_x][pad_y]. A scheduler thread
+ * admits frames into device slots carved from ONE allocation of hbm_budget_bytes (a frame
+ * waits while no slot is free), copies them to the device, and whenever frames are staged
+ * and a launch slot is free, transforms every staged frame in one persistent batched
+ * launch (up to 64 frames; two launches may be in flight), so frames that arrive while
+ * others are on the GPU join the next launch and their work overlaps. A frame's beams are
+ * bit-identical alone and in any mix. Lattice shapes: those of fftbf_batch_create.
+ * Host buffers must stay valid until the frame completes; pinned memory lets copies and
+ * transforms overlap.
+ */
+typedef struct fftbf_server fftbf_server;
+typedef struct {
+  int64_t submitted, completed;  /* frames */
+  int64_t launches;              /* batched launches issued */
+  int64_t peak_inflight;         /* most frames holding device slots at once */
+  int64_t slots;                 /* device slots the budget allows */
+  double frames_per_launch;      /* mean frames per launch */
+  double p50_ms, p99_ms, max_ms, mean_ms;  /* completion - submission, host clock */
+} fftbf_server_stats_t;
+/* n lattice plans (1..64, FP32 precision); starts the scheduler thread. NULL on error. */
+fftbf_server* fftbf_server_create(fftbf_plan* const* lattices, int n, int64_t hbm_budget_bytes);
+/* Queue one frame of lattice `lattice`; returns its ticket (>= 0) or a negative error. */
+int64_t fftbf_server_submit(fftbf_server* server, int lattice, const uint8_t* frame_host,
+                            float* beams_host);
+/* Wait until frame `ticket` (or, with ticket < 0, every submitted frame) has completed:
+ * FFTBF_OK, FFTBF_ETIMEOUT after timeout_s seconds, or the server's CUDA error. */
+int fftbf_server_wait(fftbf_server* server, int64_t ticket, double timeout_s);
+/* Counters and latency percentiles so far; returns the server's error state. */
+int fftbf_server_stats(fftbf_server* server, fftbf_server_stats_t* out);
+/* Finish queued frames, stop the scheduler, free the device slots. NULL is a no-op. */
+void fftbf_server_destroy(fftbf_server* server);
+
 /* Wait for all work the plan has enqueued; returns the first device-side error seen
  * (e.g. FFTBF_ETIMEOUT) and clears it. */
 int fftbf_plan_sync(fftbf_plan* plan);

@@ -21,7 +21,8 @@ import numpy as np
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
            "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "Batch", "batch_create",
-           "batch_execute", "batch_tuned_steps", "batch_destroy"]
+           "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
+           "server_submit", "server_wait", "server_stats", "server_destroy"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
@@ -84,6 +85,16 @@ def lib() -> ctypes.CDLL:
             L.fftbf_batch_tuned_steps.argtypes = [vp, c_int]
             L.fftbf_batch_destroy.restype = None
             L.fftbf_batch_destroy.argtypes = [vp]
+            L.fftbf_server_create.restype = vp
+            L.fftbf_server_create.argtypes = [vp, c_int, c_i64]
+            L.fftbf_server_submit.restype = c_i64
+            L.fftbf_server_submit.argtypes = [vp, c_int, vp, vp]
+            L.fftbf_server_wait.restype = c_int
+            L.fftbf_server_wait.argtypes = [vp, c_i64, ctypes.c_double]
+            L.fftbf_server_stats.restype = c_int
+            L.fftbf_server_stats.argtypes = [vp, vp]
+            L.fftbf_server_destroy.restype = None
+            L.fftbf_server_destroy.argtypes = [vp]
             L.fftbf_debug_tc_gemm.restype = c_int
             L.fftbf_debug_tc_gemm.argtypes = [vp, vp, c_int, c_int, c_int, vp, vp]
             L.fftbf_debug_unpack.restype = c_int
@@ -274,6 +285,83 @@ def batch_tuned_steps(batch: Batch, i: int) -> int:
 
 def batch_destroy(batch: Batch) -> None:
     batch.close()
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("frames_per_launch", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Server:
+    """Owning handle of an ``fftbf_server`` (continuous batching of voltage frames)."""
+
+    def __init__(self, lattices, hbm_budget_bytes):
+        self.lattices = list(lattices)
+        arr = (ctypes.c_void_p * len(self.lattices))(*[p.handle for p in self.lattices])
+        h = lib().fftbf_server_create(arr, len(self.lattices), int(hbm_budget_bytes))
+        if not h:
+            raise FftbfError(last_error_code(), last_error())
+        self.handle = h
+        self._keep = {}
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            lib().fftbf_server_destroy(h)
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def server_create(lattices, hbm_budget_bytes) -> Server:
+    return Server(lattices, hbm_budget_bytes)
+
+
+def server_submit(server: Server, lattice: int, frame: np.ndarray, beams: np.ndarray) -> int:
+    """Queue one frame (host uint8 array); the beams land in `beams` (host float32) on
+    completion. Both arrays are kept alive by the server handle until it is closed."""
+    for a in (frame, beams):
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+            raise ValueError("frames and beams must be C-contiguous numpy arrays")
+    t = lib().fftbf_server_submit(server.handle, int(lattice), frame.ctypes.data, beams.ctypes.data)
+    if t < 0:
+        raise FftbfError(int(t), last_error())
+    server._keep[t] = (frame, beams)
+    return int(t)
+
+
+def server_wait(server: Server, ticket: int = -1, timeout_s: float = 60.0) -> None:
+    _check(lib().fftbf_server_wait(server.handle, int(ticket), float(timeout_s)))
+    if ticket >= 0:
+        server._keep.pop(ticket, None)
+    else:
+        server._keep.clear()
+
+
+def server_stats(server: Server) -> dict:
+    st = ServerStats()
+    _check(lib().fftbf_server_stats(server.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def server_destroy(server: Server) -> None:
+    server.close()
 
 
 def plan_sync(plan: Plan) -> None:

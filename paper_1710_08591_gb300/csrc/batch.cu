@@ -33,12 +33,6 @@ constexpr Variant kVariants[] = {{4, 9}, {8, 7}, {16, 5}, {2, 10}, {1, 11}, {3, 
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 }  // namespace bt
 
-struct BatchJob {
-  BeamArgs a;
-  int variant;
-  int64_t item0;      // first global item of this job
-  int64_t nitems;     // nwin * nfreq
-};
 
 // One work item of one job: all its snapshots, S per step, bytes double-buffered.
 template <int MX, int LOG2N>
@@ -201,6 +195,25 @@ static size_t item_smem(const BeamArgs& a) {
                                        (size_t)a.S * a.mx * (a.my + (a.my >> 4)));
 }
 
+int batch_variant(int mx, int my) { return variant_of(mx, my); }
+
+void batch_fill_args(const fftbf_plan* p, BeamArgs& a);
+
+int batch_launch_jobs(const BatchJob* h_jobs, int njobs, BatchJob* d_jobs,
+                      unsigned long long* d_counter, size_t smem, int grid, cudaStream_t st) {
+  if (njobs < 1 || njobs > bt::kMaxJobs) return set_error(FFTBF_EINVAL, "1..%d jobs per launch", bt::kMaxJobs);
+  int64_t total = 0;
+  for (int i = 0; i < njobs; ++i) total += h_jobs[i].nitems;
+  FFTBF_CUDA_TRY(cudaMemcpyAsync(d_jobs, h_jobs, sizeof(BatchJob) * njobs, cudaMemcpyHostToDevice, st));
+  FFTBF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), st));
+  const int64_t g = total < grid ? total : grid;
+  batch_kernel<<<(unsigned)g, kThreads, smem, st>>>(d_jobs, njobs, total, d_counter);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+size_t batch_item_smem(const BeamArgs& a) { return item_smem(a); }
+
 }  // namespace fftbf
 
 using namespace fftbf;
@@ -221,6 +234,9 @@ struct fftbf_batch {
   int64_t exec_T = -1;
   std::vector<const void*> exec_ptrs;
 };
+
+static void fill_args(const fftbf_plan* p, BeamArgs& a);
+void fftbf::batch_fill_args(const fftbf_plan* p, BeamArgs& a) { fill_args(p, a); }
 
 static void fill_args(const fftbf_plan* p, BeamArgs& a) {
   a = BeamArgs{};
@@ -450,6 +466,9 @@ int fftbf_batch_execute(fftbf_batch* bb, const uint8_t* const* volts_dev, int64_
   FFTBF_CUDA_TRY(cudaGraphLaunch(bb->exec, st));
   return FFTBF_OK;
 }
+
+int fftbf_batch_grid(const fftbf_batch* bb) { return bb->nsm * bb->grid_per_sm; }
+size_t fftbf_batch_smem(const fftbf_batch* bb) { return bb->smem; }
 
 int fftbf_batch_tuned_steps(const fftbf_batch* bb, int i) {
   if (!bb || i < 0 || i >= (int)bb->plans.size()) return set_error(FFTBF_EINVAL, "bad batch index");

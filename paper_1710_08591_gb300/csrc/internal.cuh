@@ -53,6 +53,19 @@ bool fp32_n512_supported(const BeamArgs& a);
 int launch_beams_fp32_n512(const BeamArgs& a, int nsm, cudaStream_t st);
 int launch_debug_unpack(const uint8_t* in, int64_t n, float* out, cudaStream_t st);
 
+// Batched launches (batch.cu): one job = one plan's buffers over nwin windows.
+struct BatchJob {
+  BeamArgs a;
+  int variant;
+  int64_t item0;      // first global item of this job
+  int64_t nitems;     // nwin * nfreq
+};
+int batch_variant(int mx, int my);
+size_t batch_item_smem(const BeamArgs& a);
+// Upload h_jobs (item0 must be prefix sums) and run the batch kernel over them.
+int batch_launch_jobs(const BatchJob* h_jobs, int njobs, BatchJob* d_jobs,
+                      unsigned long long* d_counter, size_t smem, int grid, cudaStream_t st);
+
 // Tensor-core form (4 E-W beams x 512 N-S beams over <= 256 N-S feeds).
 struct TcArgs {
   BeamArgs b;
@@ -102,6 +115,14 @@ struct HostPipe {
 void host_pipe_free(HostPipe& hp);
 
 }  // namespace fftbf
+
+struct fftbf_plan;
+struct fftbf_batch;
+namespace fftbf {
+void batch_fill_args(const fftbf_plan* p, BeamArgs& a);
+}
+extern "C" int fftbf_batch_grid(const fftbf_batch* bb);
+extern "C" size_t fftbf_batch_smem(const fftbf_batch* bb);
 
 struct fftbf_plan {
   int device = 0;
