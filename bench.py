@@ -110,9 +110,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle ---------
-def host_block():
+def host_block(rank=0):
+    """The seeded 768-sample block of `rank`'s channel band (rank 0: the band every
+    parity test uses)."""
+    from paper_1710_08591_gb300 import multirank
+    seed = multirank.band_seed(WL["seed"], rank)
     src = synth.seeded_sources(WL["seed"] + 100, WL["n_src"], WL["amp"])
-    return synth.volts(T_HOST, WL["nfreq"], WL["npol"], WL["nx"], WL["ny"], seed=WL["seed"],
+    return synth.volts(T_HOST, WL["nfreq"], WL["npol"], WL["nx"], WL["ny"], seed=seed,
                        sigma=WL["sigma"], sources=src)
 
 
@@ -196,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     t_gen = time.perf_counter()
-    block = host_block()
+    block = host_block(rank)
     t_gen = time.perf_counter() - t_gen
     nx, ny, mx, my = WL["nx"], WL["ny"], WL["pad_x"], WL["pad_y"]
     npol, nfreq, n_int, n_tied = WL["npol"], WL["nfreq"], WL["n_int"], WL["n_tied"]
@@ -248,13 +252,11 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     kern_ms = [a.elapsed_time(b) for row in ev for a, b in row]
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    from paper_1710_08591_gb300 import multirank
+    total_ms, job_samples = multirank.aggregate(t0.elapsed_time(t1), samples_per_step() * args.steps,
+                                                device=dev)
     ms_step = total_ms / args.steps
-    value = samples_per_step() * world / (ms_step / 1e3)
+    value = multirank.throughput(total_ms, job_samples)
 
     # ---- end to end through the host-buffer entry point (pinned memory)
     e2e = None
