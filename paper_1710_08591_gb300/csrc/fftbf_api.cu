@@ -217,6 +217,8 @@ int fftbf_plan_sync(fftbf_plan* p) {
   DeviceGuard g(p->device);
   for (cudaStream_t st : p->streams_used) FFTBF_CUDA_TRY(cudaStreamSynchronize(st));
   if (p->pipe.copy) FFTBF_CUDA_TRY(cudaStreamSynchronize(p->pipe.copy));
+  for (int k = 0; k < HostPipe::kCopyStreams - 1; ++k)
+    if (p->pipe.copy_extra[k]) FFTBF_CUDA_TRY(cudaStreamSynchronize(p->pipe.copy_extra[k]));
   FFTBF_CUDA_TRY(cudaGetLastError());
   int err = 0;
   FFTBF_CUDA_TRY(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -10,6 +10,14 @@ namespace fftbf {
 
 void host_pipe_free(HostPipe& hp) {
   if (hp.copy) cudaStreamSynchronize(hp.copy);
+  for (int k = 0; k < HostPipe::kCopyStreams - 1; ++k) {
+    if (hp.copy_extra[k]) {
+      cudaStreamSynchronize(hp.copy_extra[k]);
+      cudaStreamDestroy(hp.copy_extra[k]);
+    }
+    for (int b = 0; b < 2; ++b)
+      if (hp.copied_extra[b][k]) cudaEventDestroy(hp.copied_extra[b][k]);
+  }
   for (int b = 0; b < 2; ++b) {
     if (hp.copied[b]) cudaEventDestroy(hp.copied[b]);
     if (hp.freed[b]) cudaEventDestroy(hp.freed[b]);
@@ -65,6 +73,11 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
       FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.copied[b], cudaEventDisableTiming));
       FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.freed[b], cudaEventDisableTiming));
     }
+    for (int k = 0; k < HostPipe::kCopyStreams - 1; ++k) {
+      FFTBF_CUDA_TRY(cudaStreamCreateWithFlags(&hp.copy_extra[k], cudaStreamNonBlocking));
+      for (int b = 0; b < 2; ++b)
+        FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.copied_extra[b][k], cudaEventDisableTiming));
+    }
   }
   const int64_t nwin = T / p->n_int;
   const size_t snap_t = (size_t)p->nfreq * p->npol * p->nx * p->ny;   // bytes per sample t
@@ -74,12 +87,11 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
   int64_t cw = (int64_t)((256ull << 20) / win_bytes);
   if (cw < 1) cw = 1;
   if (cw > nwin) cw = nwin;
-  for (int b = 0; b < 2; ++b) {
-    if (hp.stage_bytes < cw * win_bytes) {
-      // all earlier work on the old buffers must be done before they are freed
-      cudaStreamSynchronize(hp.copy);
-      cudaStreamSynchronize(st);
-    }
+  if (hp.stage_bytes < cw * win_bytes) {
+    // all earlier work on the old buffers must be done before they are freed
+    cudaStreamSynchronize(hp.copy);
+    for (int k = 0; k < HostPipe::kCopyStreams - 1; ++k) cudaStreamSynchronize(hp.copy_extra[k]);
+    cudaStreamSynchronize(st);
   }
   if (hp.stage_bytes < cw * win_bytes) {
     for (int b = 0; b < 2; ++b) {
@@ -111,11 +123,24 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
   for (int64_t w0 = 0; w0 < nwin; w0 += cw, ++chunk) {
     const int b = chunk & 1;
     const int64_t nw = std::min<int64_t>(cw, nwin - w0);
-    FFTBF_CUDA_TRY(cudaStreamWaitEvent(hp.copy, hp.freed[b], 0));
-    FFTBF_CUDA_TRY(cudaMemcpyAsync(hp.stage[b], volts_h + w0 * win_bytes, nw * win_bytes,
-                                   cudaMemcpyHostToDevice, hp.copy));
-    FFTBF_CUDA_TRY(cudaEventRecord(hp.copied[b], hp.copy));
-    FFTBF_CUDA_TRY(cudaStreamWaitEvent(st, hp.copied[b], 0));
+    // the chunk's bytes go over kCopyStreams concurrent copies (one engine rarely fills
+    // the host link), each waiting until the previous user of buffer b has finished
+    const size_t bytes = nw * win_bytes;
+    const size_t part = ((bytes / HostPipe::kCopyStreams) + 4095) & ~(size_t)4095;
+    for (int k = 0; k < HostPipe::kCopyStreams; ++k) {
+      cudaStream_t cs = k == 0 ? hp.copy : hp.copy_extra[k - 1];
+      cudaEvent_t ev = k == 0 ? hp.copied[b] : hp.copied_extra[b][k - 1];
+      const size_t off = (size_t)k * part;
+      if (off >= bytes) {
+        FFTBF_CUDA_TRY(cudaEventRecord(ev, cs));
+      } else {
+        FFTBF_CUDA_TRY(cudaStreamWaitEvent(cs, hp.freed[b], 0));
+        FFTBF_CUDA_TRY(cudaMemcpyAsync(hp.stage[b] + off, volts_h + w0 * win_bytes + off,
+                                       std::min(part, bytes - off), cudaMemcpyHostToDevice, cs));
+        FFTBF_CUDA_TRY(cudaEventRecord(ev, cs));
+      }
+      FFTBF_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+    }
     rc = fftbf_execute(p, hp.stage[b], nw * p->n_int, hp.beams + w0 * beam_win, stream);
     if (rc != FFTBF_OK) return rc;
     FFTBF_CUDA_TRY(cudaEventRecord(hp.freed[b], st));

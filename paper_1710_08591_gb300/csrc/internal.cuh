@@ -102,7 +102,10 @@ void tied_free(TiedTables& tt);
 
 // Staging of fftbf_execute_host: two voltage chunks, device outputs, copy stream.
 struct HostPipe {
+  static constexpr int kCopyStreams = 4;   // parallel host-to-device copies per chunk
   cudaStream_t copy = nullptr;
+  cudaStream_t copy_extra[kCopyStreams - 1] = {nullptr, nullptr, nullptr};
+  cudaEvent_t copied_extra[2][kCopyStreams - 1] = {};
   cudaEvent_t copied[2] = {nullptr, nullptr};
   cudaEvent_t freed[2] = {nullptr, nullptr};
   uint8_t* stage[2] = {nullptr, nullptr};
