@@ -251,3 +251,73 @@ def tied_direct(x, w, u, v, n_int) -> np.ndarray:
     y = np.einsum("tfpxy,fsx,fsy->tfps", wx, ex, ey)
     inten = (y.real ** 2 + y.imag ** 2).sum(axis=2)
     return inten.reshape(T // n_int, n_int, F, -1).sum(axis=1)
+
+
+# --- intensity-space windowing (optimal windowed beams) --------------------------------
+def window_lag_coeffs(h) -> np.ndarray:
+    """g_delta for delta = -(n-1) .. n-1 (index delta + n - 1) of the optimal windowed beam
+    (Eq. w_opt): the window's auto-convolution sum_alpha h^(alpha+delta) h^(alpha*) divided
+    by the n - |delta| redundant baselines. Unnormalised: a flat window gives g = 1, i.e.
+    the plain pointed beam. Real windows give real, symmetric g."""
+    h = np.asarray(h, dtype=np.complex128)
+    n = h.size
+    g = np.zeros(2 * n - 1, dtype=np.complex128)
+    for d in range(-(n - 1), n):
+        acc = 0j
+        for a in range(max(0, -d), min(n, n - d)):
+            acc += h[a + d] * np.conj(h[a])
+        g[d + n - 1] = acc / (n - abs(d))
+    return g
+
+
+def windowed_regrid_weights(n: int, m: int, y, g) -> np.ndarray:
+    """FFT-beam coefficients of the optimal windowed beam pointed at y (M >= 2n - 1):
+    w^A = (1/M) sum_delta g_delta exp(-2 pi i delta (y - A/M)) (Eq. wA_from_wdelta applied to
+    the lag weights of Eq. w_opt, in this library's unnormalised convention). Real part
+    returned (g of a real window is symmetric, so the sum is real)."""
+    y = np.asarray(y, dtype=np.float64)
+    if m < 2 * n - 1:
+        raise ValueError("windowed regridding needs M >= 2n - 1")
+    yy = y[..., None] - np.arange(m, dtype=np.float64) / m
+    acc = np.zeros(yy.shape, dtype=np.complex128)
+    for d in range(-(n - 1), n):
+        acc += g[d + n - 1] * np.exp(-1j * TWO_PI * d * yy)
+    return acc.real / m
+
+
+def tied_windowed_regrid(P, u, v, nx, ny, hx, hy) -> np.ndarray:
+    """Optimal windowed tied beams from FFT-beam intensities, separable window hx x hy."""
+    P = np.asarray(P, dtype=np.float64)
+    mx, my = P.shape[-2:]
+    wx = windowed_regrid_weights(nx, mx, u, window_lag_coeffs(hx))
+    wy = windowed_regrid_weights(ny, my, v, window_lag_coeffs(hy))
+    return np.einsum("fsA,fsB,jfAB->jfs", wx, wy, P)
+
+
+def tied_windowed_visibility(x, w, u, v, n_int, hx, hy) -> np.ndarray:
+    """The same beams formed directly in redundancy-stacked visibility space:
+    T = sum_delta g_delta exp(-2 pi i (dx u + dy v)) V~_delta (Eq. b_V_delta with the
+    optimal windowed lag weights of Eq. w_opt). Tiny lattices only."""
+    x = np.asarray(x)
+    nx, ny = x.shape[-2:]
+    S = stacked_visibilities(x, w, n_int)                     # [J, F, 2nx-1, 2ny-1]
+    gx, gy = window_lag_coeffs(hx), window_lag_coeffs(hy)
+    dxs = np.arange(-(nx - 1), nx)
+    dys = np.arange(-(ny - 1), ny)
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    ex = gx[None, None, :] * np.exp(-1j * TWO_PI * u[:, :, None] * dxs[None, None, :])
+    ey = gy[None, None, :] * np.exp(-1j * TWO_PI * v[:, :, None] * dys[None, None, :])
+    return np.einsum("fsd,fse,jfde->jfs", ex, ey, S).real
+
+
+def truncate_nearest(weights, y, m, k) -> np.ndarray:
+    """Keep the regridding weights of the k FFT beams nearest to the pointing, zero the
+    rest: beams A = first .. first + k - 1 (mod M) with first = floor(y M - (k - 1)/2 + 1/2).
+    This is the compact kernel of Section 4.1 (a windowed beam needs only a few FFT beams)."""
+    w = np.array(weights, dtype=np.float64, copy=True)
+    y = np.asarray(y, dtype=np.float64)
+    first = np.floor(y * m - (k - 1) / 2.0 + 0.5)
+    rel = np.mod(np.arange(m, dtype=np.float64) - first[..., None], m)
+    w[rel >= k] = 0.0
+    return w
