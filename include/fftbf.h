@@ -123,6 +123,27 @@ int fftbf_tied_beams(fftbf_plan* plan, const float* beams_dev, int64_t n_windows
                      void* stream);
 
 /*
+ * Shape the tied beams of later fftbf_tied_beams calls in intensity space (Section 4.1):
+ * with a real window h on an axis, the tied beam becomes the optimal windowed beam whose
+ * redundant-baseline weights are g_delta = sum_alpha h^(alpha+delta) h^alpha /
+ * (n - |delta|) (Eq. w_opt, unnormalised: a flat window is the plain pointed beam), so
+ * the regridding coefficients are w^A(y) = (1/M) sum_delta g_delta
+ * exp(-2 pi i delta (y - A/M)) (Eq. wA_from_wdelta). A window needs pad >= 2n - 1 on its
+ * axis (FFTBF_EINVAL otherwise).
+ *   hx, hy     host double windows of nx and ny values, or NULL for no window on that
+ *              axis (Dirichlet kernel of Eq. bp_max_arbitrary). Copied.
+ *   trunc_x/y  keep only the `trunc` FFT beams nearest the pointing (beams
+ *              floor(y M - (trunc-1)/2 + 1/2) .. + trunc-1, cyclic) and drop the rest: the
+ *              compact kernel a windowed beam allows (Section 4.1); 0 keeps every beam.
+ *              When both axes have few taps (truncated, or a grid axis with pad < 2n-1)
+ *              the tied beams use a gather kernel of trunc_x x trunc_y taps instead of the
+ *              GEMM over all FFT beams.
+ * Takes effect at the next fftbf_tied_beams call (tables are rebuilt).
+ */
+int fftbf_tied_set_window(fftbf_plan* plan, const double* hx, const double* hy, int trunc_x,
+                          int trunc_y);
+
+/*
  * The same pass as fftbf_execute followed by fftbf_tied_beams, on HOST buffers: the
  * voltages are copied to the device in window-sized chunks on a copy stream owned by
  * the plan, overlapped with the transform of the previous chunk on `stream`; the

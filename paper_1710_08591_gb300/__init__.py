@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
-           "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams",
+           "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window",
            "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "Batch", "batch_create",
            "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
            "server_submit", "server_wait", "server_stats", "server_destroy"]
@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
             L.fftbf_execute.argtypes = [vp, vp, c_i64, vp, vp]
             L.fftbf_tied_beams.restype = c_int
             L.fftbf_tied_beams.argtypes = [vp, vp, c_i64, c_int, vp, vp, vp, vp]
+            L.fftbf_tied_set_window.restype = c_int
+            L.fftbf_tied_set_window.argtypes = [vp, vp, vp, c_int, c_int]
             L.fftbf_execute_host.restype = c_int
             L.fftbf_execute_host.argtypes = [vp, vp, c_i64, vp, c_int, vp, vp, vp, vp]
             L.fftbf_plan_sync.restype = c_int
@@ -214,6 +216,15 @@ def tied_beams(plan: Plan, beams, n_windows: int, n_tied: int, u, v, tied, strea
     uu, vv = _host_f64(u, n), _host_f64(v, n)
     _check(lib().fftbf_tied_beams(plan.handle, _dptr(beams), int(n_windows), int(n_tied),
                                   uu.ctypes.data, vv.ctypes.data, _dptr(tied), _stream(stream)))
+
+
+def tied_set_window(plan: Plan, hx=None, hy=None, trunc_x: int = 0, trunc_y: int = 0) -> None:
+    """Optimal windowed tied beams (real windows per axis) and/or truncated kernels."""
+    ax = None if hx is None else _host_f64(hx, plan.nx)
+    ay = None if hy is None else _host_f64(hy, plan.ny)
+    _check(lib().fftbf_tied_set_window(plan.handle, None if ax is None else ax.ctypes.data,
+                                       None if ay is None else ay.ctypes.data, int(trunc_x),
+                                       int(trunc_y)))
 
 
 def execute_host(plan: Plan, volts: np.ndarray, T: int, beams: np.ndarray, n_tied: int = 0,

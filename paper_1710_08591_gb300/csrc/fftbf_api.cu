@@ -212,6 +212,41 @@ int fftbf_tied_beams(fftbf_plan* p, const float* beams, int64_t n_windows, int n
   return rc;
 }
 
+int fftbf_tied_set_window(fftbf_plan* p, const double* hx, const double* hy, int trunc_x,
+                          int trunc_y) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  if (trunc_x < 0 || trunc_y < 0 || trunc_x > p->mx || trunc_y > p->my)
+    return set_error(FFTBF_EINVAL, "truncation must be in 0..pad per axis");
+  if (hx && p->mx < 2 * p->nx - 1)
+    return set_error(FFTBF_EINVAL, "an E-W window needs pad_x >= 2nx-1 (the FFT beams of a "
+                     "smaller padding do not hold every redundant baseline)");
+  if (hy && p->my < 2 * p->ny - 1)
+    return set_error(FFTBF_EINVAL, "a N-S window needs pad_y >= 2ny-1");
+  auto lags = [](const double* h, int n, std::vector<double>& g) -> int {
+    g.clear();
+    if (!h) return FFTBF_OK;
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(h[i])) return set_error(FFTBF_EINVAL, "window value %d not finite", i);
+    g.assign(2 * (size_t)n - 1, 0.0);
+    for (int d = -(n - 1); d < n; ++d) {
+      double acc = 0.0;
+      for (int a = std::max(0, -d); a < std::min(n, n - d); ++a) acc += h[a + d] * h[a];
+      g[d + n - 1] = acc / (n - std::abs(d));
+    }
+    return FFTBF_OK;
+  };
+  std::vector<double> gx, gy;
+  int rc = lags(hx, p->nx, gx);
+  if (rc == FFTBF_OK) rc = lags(hy, p->ny, gy);
+  if (rc != FFTBF_OK) return rc;
+  p->tied.win_x.g.swap(gx);
+  p->tied.win_y.g.swap(gy);
+  p->tied.win_x.trunc = trunc_x;
+  p->tied.win_y.trunc = trunc_y;
+  ++p->tied.version;
+  return FFTBF_OK;
+}
+
 int fftbf_plan_sync(fftbf_plan* p) {
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   DeviceGuard g(p->device);

@@ -84,10 +84,21 @@ int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16,
 int build_tables(int nx, int mx, int my, float2* ex, float2* tw, cudaStream_t st);
 
 // Tied-beam weight tables and regridding GEMM.
+struct AxisWindow {
+  std::vector<double> g;        // 2n-1 lag coefficients of the optimal windowed beam; empty = none
+  int trunc = 0;                // keep the `trunc` FFT beams nearest the pointing (0 = all)
+};
 struct TiedTables {
   int n_tied = 0;
+  AxisWindow win_x, win_y;
+  int version = 0, built_version = -1;   // window settings the tables were built for
+  double* d_g = nullptr;        // device copy: g_x then g_y
+  int kx = 0, ky = 0;           // compact kernel taps per axis (0: dense GEMM path)
+  int* first = nullptr;         // [nfreq][n_tied][2] first kept beam per axis (compact path)
+  float* cw = nullptr;          // [nfreq][n_tied][kx + ky] tap weights (compact path)
   std::vector<double> u, v;     // host copies of the pointings the tables were made for
   std::vector<int> hperm;       // host copy of perm
+  std::vector<double> hg;       // host staging of the lag coefficients
   float* wx = nullptr;          // [nfreq][n_tied][mx] in sorted order
   float* wy = nullptr;          // [nfreq][n_tied][my] in sorted order
   int* perm = nullptr;          // [nfreq][n_tied] sorted slot -> caller's pointing index

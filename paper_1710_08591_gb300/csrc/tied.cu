@@ -19,22 +19,51 @@
 
 namespace fftbf {
 
+// Axis modes: 0 = Dirichlet kernel (M >= 2n-1), 1 = the FFT beam itself (M < 2n-1, on
+// grid), 2 = optimal windowed kernel from lag coefficients g (M >= 2n-1).
 // FP64 regridding weight of beam k on an axis of n feeds and M beams for pointing y.
-__device__ __forceinline__ double regrid_weight(int n, int M, bool dense, double y, int k) {
-  if (dense) {
+__device__ __forceinline__ double regrid_weight(int n, int M, int mode, const double* g,
+                                                double y, int k) {
+  if (mode == 0) {
     double e = y - (double)k / (double)M;
     e -= rint(e);                          // the kernel has period 1 in y
     const double L = 2.0 * n - 1.0;
     if (fabs(e) < 1e-9) return L / M;      // limit at y - k/M integer (error ~ n^2 e^2)
     return sinpi(L * e) / (sinpi(e) * (double)M);
   }
-  long long k0 = llrint(y * (double)M) % M;
-  if (k0 < 0) k0 += M;
-  return k0 == k ? 1.0 : 0.0;
+  if (mode == 1) {
+    long long k0 = llrint(y * (double)M) % M;
+    if (k0 < 0) k0 += M;
+    return k0 == k ? 1.0 : 0.0;
+  }
+  // (1/M) sum_delta g_delta exp(-2 pi i delta e): powers of z = exp(-2 pi i e) by rotation
+  double e = y - (double)k / (double)M;
+  e -= rint(e);
+  double zs, zc;
+  sincospi(-2.0 * e, &zs, &zc);
+  double pr = 1.0, pi = 0.0, acc = g[n - 1];
+  for (int d = 1; d < n; ++d) {
+    const double r = pr * zc - pi * zs;
+    pi = pr * zs + pi * zc;
+    pr = r;
+    acc += (g[n - 1 + d] + g[n - 1 - d]) * pr;   // real, symmetric lag weights
+  }
+  return acc / M;
 }
 
-__global__ void tied_table_kernel(int n, int M, int dense, int nfreq, int n_tied,
-                                  const double* y, const int* perm, float* out) {
+// First kept beam of a truncated kernel of `k` taps (k nearest beams to y M).
+__device__ __forceinline__ int first_tap(int M, int mode, double y, int k) {
+  long long f0;
+  if (mode == 1) f0 = llrint(y * (double)M);
+  else f0 = (long long)floor(y * (double)M - 0.5 * (k - 1) + 0.5);
+  f0 %= M;
+  if (f0 < 0) f0 += M;
+  return (int)f0;
+}
+
+__global__ void tied_table_kernel(int n, int M, int mode, const double* g, int trunc,
+                                  int nfreq, int n_tied, const double* y, const int* perm,
+                                  float* out) {
   const int64_t total = (int64_t)nfreq * n_tied * M;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -42,7 +71,61 @@ __global__ void tied_table_kernel(int n, int M, int dense, int nfreq, int n_tied
     const int64_t fs = i / M;                         // f * n_tied + sorted slot
     const int f = (int)(fs / n_tied);
     const int s = perm[fs];
-    out[i] = (float)regrid_weight(n, M, dense != 0, y[(int64_t)f * n_tied + s], k);
+    const double yv = y[(int64_t)f * n_tied + s];
+    double w = regrid_weight(n, M, mode, g, yv, k);
+    if (trunc > 0 && mode != 1) {
+      const int rel = (k - first_tap(M, mode, yv, trunc) + M) % M;
+      if (rel >= trunc) w = 0.0;
+    }
+    out[i] = (float)w;
+  }
+}
+
+// Compact tables: per (f, pointing) the first kept beam of each axis and the kx + ky tap
+// weights (caller's pointing order).
+__global__ void tied_compact_table_kernel(int nx, int ny, int mx, int my, int mode_x,
+                                          int mode_y, const double* gx, const double* gy,
+                                          int kx, int ky, int nfreq, int n_tied,
+                                          const double* u, const double* v, int* first,
+                                          float* cw) {
+  const int64_t total = (int64_t)nfreq * n_tied;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int fx = first_tap(mx, mode_x, u[i], kx), fy = first_tap(my, mode_y, v[i], ky);
+    first[2 * i] = fx;
+    first[2 * i + 1] = fy;
+    float* c = cw + i * (kx + ky);
+    for (int t = 0; t < kx; ++t) c[t] = (float)regrid_weight(nx, mx, mode_x, gx, u[i], (fx + t) % mx);
+    for (int t = 0; t < ky; ++t) c[kx + t] = (float)regrid_weight(ny, my, mode_y, gy, v[i], (fy + t) % my);
+  }
+}
+
+// out[j,f,s] = sum_{tx<kx, ty<ky} cx[tx] cy[ty] P[j,f,(fx+tx) mod Mx,(fy+ty) mod My]: one
+// thread per (window, channel, pointing), pointings fastest so a CTA shares P[j,f].
+__global__ void __launch_bounds__(256) tied_compact_kernel(const float* __restrict__ P,
+                                                            const int* __restrict__ first,
+                                                            const float* __restrict__ cw,
+                                                            float* __restrict__ out, int64_t nwin,
+                                                            int nfreq, int n_tied, int mx,
+                                                            int my, int kx, int ky) {
+  const int64_t total = nwin * nfreq * (int64_t)n_tied;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t jf = i / n_tied;
+    const int s = (int)(i - jf * n_tied);
+    const int f = (int)(jf % nfreq);
+    const int64_t fs = (int64_t)f * n_tied + s;
+    const float* Pj = P + jf * (int64_t)(mx * my);
+    const float* c = cw + fs * (kx + ky);
+    const int fx = first[2 * fs], fy = first[2 * fs + 1];
+    float acc = 0.f;
+    for (int tx = 0; tx < kx; ++tx) {
+      const float* row = Pj + ((fx + tx) % mx) * my;
+      float racc = 0.f;
+      for (int ty = 0; ty < ky; ++ty) racc = fmaf(c[kx + ty], __ldg(row + (fy + ty) % my), racc);
+      acc = fmaf(c[tx], racc, acc);
+    }
+    out[i] = acc;
   }
 }
 
@@ -123,18 +206,26 @@ void tied_free(TiedTables& tt) {
   cudaFree(tt.wy);
   cudaFree(tt.perm);
   cudaFree(tt.duv);
+  cudaFree(tt.d_g);
+  cudaFree(tt.first);
+  cudaFree(tt.cw);
   tt = TiedTables();
 }
 
 int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int n_tied,
                  const double* u, const double* v, cudaStream_t st) {
   const size_t nuv = (size_t)nfreq * n_tied;
-  if (tt.n_tied == n_tied && tt.u.size() == nuv &&
+  if (tt.n_tied == n_tied && tt.u.size() == nuv && tt.built_version == tt.version &&
       std::memcmp(tt.u.data(), u, nuv * sizeof(double)) == 0 &&
       std::memcmp(tt.v.data(), v, nuv * sizeof(double)) == 0)
     return FFTBF_OK;                                  // same pointings: tables are current
 
   const bool dense_x = mx >= 2 * nx - 1, dense_y = my >= 2 * ny - 1;
+  const int mode_x = !dense_x ? 1 : (tt.win_x.g.empty() ? 0 : 2);
+  const int mode_y = !dense_y ? 1 : (tt.win_y.g.empty() ? 0 : 2);
+  // compact path when both axes use a few taps: a grid axis (1 tap) or a truncated kernel
+  const int kx = mode_x == 1 ? 1 : tt.win_x.trunc, ky = mode_y == 1 ? 1 : tt.win_y.trunc;
+  const bool compact = kx > 0 && ky > 0;
   for (size_t i = 0; i < nuv; ++i) {
     if (!std::isfinite(u[i]) || !std::isfinite(v[i]))
       return set_error(FFTBF_EINVAL, "tied pointing %zu is not finite", i);
@@ -161,25 +252,36 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
       });
     }
   }
-  if (tt.cap_tied < nuv || tt.n_tied != n_tied) {
-    cudaFree(tt.wx);
-    cudaFree(tt.wy);
-    cudaFree(tt.perm);
-    cudaFree(tt.duv);
-    tt.wx = tt.wy = nullptr;
-    tt.perm = nullptr;
-    tt.duv = nullptr;
-    tt.cap_tied = 0;
-    if (cudaMalloc(&tt.wx, nuv * mx * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&tt.wy, nuv * my * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&tt.perm, nuv * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&tt.duv, 2 * nuv * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
-      tied_free(tt);
-      return set_error(FFTBF_ENOMEM, "cannot allocate tied-beam tables (%zu pointings)", nuv);
-    }
-    tt.cap_tied = nuv;
+  // (re)allocate the tables of the path in use
+  cudaFree(tt.wx);
+  cudaFree(tt.wy);
+  cudaFree(tt.perm);
+  cudaFree(tt.duv);
+  cudaFree(tt.d_g);
+  cudaFree(tt.first);
+  cudaFree(tt.cw);
+  tt.wx = tt.wy = tt.cw = nullptr;
+  tt.perm = tt.first = nullptr;
+  tt.duv = tt.d_g = nullptr;
+  tt.cap_tied = 0;
+  const size_t ng = tt.win_x.g.size() + tt.win_y.g.size();
+  bool ok = cudaMalloc(&tt.perm, nuv * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&tt.duv, 2 * nuv * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&tt.d_g, (ng ? ng : 1) * sizeof(double)) == cudaSuccess;
+  if (ok && compact)
+    ok = cudaMalloc(&tt.first, 2 * nuv * sizeof(int)) == cudaSuccess &&
+         cudaMalloc(&tt.cw, nuv * (kx + ky) * sizeof(float)) == cudaSuccess;
+  if (ok && !compact)
+    ok = cudaMalloc(&tt.wx, nuv * mx * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&tt.wy, nuv * my * sizeof(float)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    tied_free(tt);
+    return set_error(FFTBF_ENOMEM, "cannot allocate tied-beam tables (%zu pointings)", nuv);
   }
+  tt.cap_tied = nuv;
+  tt.kx = compact ? kx : 0;
+  tt.ky = compact ? ky : 0;
   // The plan keeps host copies of the pointings (to detect a repeat) and of the order;
   // the uploads read those plan-owned buffers, never the caller's.
   tt.n_tied = 0;
@@ -189,14 +291,29 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
   FFTBF_CUDA_TRY(cudaMemcpyAsync(tt.duv, tt.u.data(), nuv * sizeof(double), cudaMemcpyHostToDevice, st));
   FFTBF_CUDA_TRY(cudaMemcpyAsync(tt.duv + nuv, tt.v.data(), nuv * sizeof(double), cudaMemcpyHostToDevice, st));
   FFTBF_CUDA_TRY(cudaMemcpyAsync(tt.perm, tt.hperm.data(), nuv * sizeof(int), cudaMemcpyHostToDevice, st));
+  tt.hg.assign(tt.win_x.g.begin(), tt.win_x.g.end());
+  tt.hg.insert(tt.hg.end(), tt.win_y.g.begin(), tt.win_y.g.end());
+  if (!tt.hg.empty())
+    FFTBF_CUDA_TRY(cudaMemcpyAsync(tt.d_g, tt.hg.data(), tt.hg.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, st));
+  const double* gx = tt.d_g;
+  const double* gy = tt.d_g + tt.win_x.g.size();
   const int threads = 256;
   auto blocks = [&](int64_t n) { return (unsigned)std::min<int64_t>((n + threads - 1) / threads, 1 << 20); };
-  tied_table_kernel<<<blocks((int64_t)nuv * mx), threads, 0, st>>>(nx, mx, dense_x, nfreq,
-                                                                    n_tied, tt.duv, tt.perm, tt.wx);
-  FFTBF_CUDA_TRY(cudaGetLastError());
-  tied_table_kernel<<<blocks((int64_t)nuv * my), threads, 0, st>>>(ny, my, dense_y, nfreq,
-                                                                    n_tied, tt.duv + nuv, tt.perm, tt.wy);
-  FFTBF_CUDA_TRY(cudaGetLastError());
+  if (compact) {
+    tied_compact_table_kernel<<<blocks((int64_t)nuv), threads, 0, st>>>(
+        nx, ny, mx, my, mode_x, mode_y, gx, gy, kx, ky, nfreq, n_tied, tt.duv, tt.duv + nuv,
+        tt.first, tt.cw);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+  } else {
+    tied_table_kernel<<<blocks((int64_t)nuv * mx), threads, 0, st>>>(
+        nx, mx, mode_x, gx, tt.win_x.trunc, nfreq, n_tied, tt.duv, tt.perm, tt.wx);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+    tied_table_kernel<<<blocks((int64_t)nuv * my), threads, 0, st>>>(
+        ny, my, mode_y, gy, tt.win_y.trunc, nfreq, n_tied, tt.duv + nuv, tt.perm, tt.wy);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+  }
+  tt.built_version = tt.version;
   tt.n_tied = n_tied;
   return FFTBF_OK;
 }
@@ -204,6 +321,14 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
 int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
                 int my, float* out, cudaStream_t st) {
   if (nwin <= 0) return FFTBF_OK;
+  if (tt.kx > 0 && tt.ky > 0) {
+    const int64_t total = nwin * nfreq * (int64_t)tt.n_tied;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
+    tied_compact_kernel<<<blocks, 256, 0, st>>>(beams, tt.first, tt.cw, out, nwin, nfreq,
+                                                tt.n_tied, mx, my, tt.kx, tt.ky);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+    return FFTBF_OK;
+  }
   const int64_t jt = (nwin + TJ - 1) / TJ;
   if (jt > 65535 || nfreq > 65535)
     return set_error(FFTBF_EUNSUPPORTED, "tied beams: too many windows or channels per call");
