@@ -339,6 +339,32 @@ def run_ours(args, rank, world, local_rank):
             forms[form] = {"value": samples_per_step() * world / (fms / 1e3), "ms_per_step": fms}
             fplan.close()
 
+    # ---- tied-beam variants on the step's 128 windows: plain (Dirichlet, GEMM over the 512
+    # N-S beams), optimal half-sine window (GEMM), the same window truncated to 5 taps
+    tied_forms = None
+    if not args.no_forms:
+        tied_forms = {}
+        ref_dense = None
+        for name, hy, trunc in (("plain_gemm", None, 0), ("window_gemm", synth.half_sine(ny), 0),
+                                ("window_5tap", synth.half_sine(ny), 5)):
+            fb.tied_set_window(plan, None, hy, 0, trunc)
+            fb.tied_beams(plan, beams, nwin, n_tied, u, v, tied, stream)     # builds the tables
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(3):
+                fb.tied_beams(plan, beams, nwin, n_tied, u, v, tied, stream)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            tied_forms[name] = {"ms": a0.elapsed_time(a1) / 3}
+            if name == "window_gemm":
+                ref_dense = tied.clone()
+            if name == "window_5tap":
+                rel = (tied - ref_dense).abs() / ref_dense.abs().clamp_min(1e-30)
+                tied_forms[name]["max_rel_vs_all_beams"] = float(rel.max())
+                tied_forms[name]["median_rel_vs_all_beams"] = float(rel.flatten()[:1 << 24].median())
+        fb.tied_set_window(plan)
+
     serving = None
     if not args.no_serving:
         serving = run_serving(fb, torch, dev, frames_total=args.serve_frames)
@@ -363,7 +389,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"{world} GPU(s), independent channel bands per GPU"},
             "gpu_launches": (ncall + 1) * args.steps,
             "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "forms": forms, "serving": serving}
+            "forms": forms, "tied_beams": tied_forms, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
