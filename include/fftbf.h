@@ -253,6 +253,14 @@ int fftbf_debug_tc_gemm(const uint16_t* a_dev, const uint16_t* b_dev, int n, int
                         int padded, float* d_dev, void* stream);
 
 /*
+ * Test hook for failure detection without a GPU fault: a kernel waits, with the same
+ * bounded wait the tensor-core kernels use, on an mbarrier that nothing arrives on. The
+ * wait gives up after limit_us microseconds of device time (1..2000000) and the call
+ * returns FFTBF_ETIMEOUT; the CUDA context stays usable. Synchronises `stream`.
+ */
+int fftbf_debug_wait_timeout(int limit_us, void* stream);
+
+/*
  * fftbf_execute without a plan and without any device allocation. The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc, such
  * as an application that hands all device memory to its own pool before it starts

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window",
-           "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "Batch", "batch_create",
+           "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "Batch", "batch_create",
            "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
            "server_submit", "server_wait", "server_stats", "server_destroy"]
 
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
             L.fftbf_server_stats.argtypes = [vp, vp]
             L.fftbf_server_destroy.restype = None
             L.fftbf_server_destroy.argtypes = [vp]
+            L.fftbf_debug_wait_timeout.restype = c_int
+            L.fftbf_debug_wait_timeout.argtypes = [c_int, vp]
             L.fftbf_debug_tc_gemm.restype = c_int
             L.fftbf_debug_tc_gemm.argtypes = [vp, vp, c_int, c_int, c_int, vp, vp]
             L.fftbf_debug_unpack.restype = c_int
@@ -389,6 +391,11 @@ def execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights, volts, T:
     memory); weights is a device tensor of nx*ny complex64 values or None."""
     _check(lib().fftbf_execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, _dptr(weights),
                                        _dptr(volts), int(T), _dptr(beams), _stream(stream)))
+
+
+def debug_wait_timeout(limit_us: int, stream=None) -> int:
+    """Run the bounded-wait test kernel; returns the status (FFTBF_ETIMEOUT expected)."""
+    return int(lib().fftbf_debug_wait_timeout(int(limit_us), _stream(stream)))
 
 
 def debug_tc_gemm(a, b, n: int, bf16: bool, padded: bool, d, stream=None) -> None:

@@ -770,6 +770,25 @@ __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A
   if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
+// Wait, with the kernels' bounded wait, on an mbarrier that nothing arrives on: the wait
+// runs out after limit_ns and the kernel records FFTBF_ETIMEOUT instead of hanging.
+__global__ void debug_wait_timeout_kernel(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = tc::mbar_wait(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicExch(err, FFTBF_ETIMEOUT);
+}
+
+int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st) {
+  debug_wait_timeout_kernel<<<1, 32, 0, st>>>(limit_ns, err);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
 int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
                          float* D, int* err, cudaStream_t st) {
   const int asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;

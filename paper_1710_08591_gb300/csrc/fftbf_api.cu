@@ -287,6 +287,23 @@ int fftbf_debug_unpack(const uint8_t* in, int64_t n, float* out, void* stream) {
   return launch_debug_unpack(in, n, out, static_cast<cudaStream_t>(stream));
 }
 
+int fftbf_debug_wait_timeout(int limit_us, void* stream) {
+  if (limit_us < 1 || limit_us > 2000000) return set_error(FFTBF_EINVAL, "limit_us must be 1..2000000");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* err = nullptr;
+  FFTBF_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  int rc = FFTBF_OK;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) rc = launch_debug_wait_timeout((uint64_t)limit_us * 1000ull, err, st);
+  int h = 0;
+  if (e == cudaSuccess && rc == FFTBF_OK) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && rc == FFTBF_OK) e = cudaStreamSynchronize(st);
+  cudaFree(err);
+  if (e != cudaSuccess) return cuda_error(e, "debug wait");
+  if (rc != FFTBF_OK) return rc;
+  return h ? set_error(h, "device wait ran out after %d us (as intended)", limit_us) : FFTBF_OK;
+}
+
 int fftbf_debug_tc_gemm(const uint16_t* a, const uint16_t* b, int n, int bf16, int padded,
                         float* d, void* stream) {
   if (!a || !b || !d) return set_error(FFTBF_EINVAL, "null pointer");

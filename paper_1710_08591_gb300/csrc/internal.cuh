@@ -80,6 +80,7 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st);
 int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st);
 int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
                          float* D, int* err, cudaStream_t st);
+int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st);
 // FP64 table builders (device), rounded to FP32.
 int build_tables(int nx, int mx, int my, float2* ex, float2* tw, cudaStream_t st);
 
