@@ -367,6 +367,19 @@ def run_ours(args, rank, world, local_rank):
                 tied_forms[name]["max_err_vs_all_beams"] = float(rel.max())
                 tied_forms[name]["rms_err_vs_all_beams"] = float(rel.pow(2).mean().sqrt())
         fb.tied_set_window(plan)
+        # redundancy-stacked visibilities from the same FFT beams (N-S lags, E-W beams kept)
+        sdx, sdy = fb.stacked_shape(plan)
+        vis = torch.empty((nwin, nfreq, sdx, sdy), dtype=torch.complex64, device=dev)
+        fb.stacked_visibilities(plan, beams, nwin, vis, stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a0.record(stream)
+        for _ in range(3):
+            fb.stacked_visibilities(plan, beams, nwin, vis, stream)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        tied_forms["stacked_visibilities"] = {"ms": a0.elapsed_time(a1) / 3, "shape": [sdx, sdy]}
+        del vis
 
     serving = None
     if not args.no_serving:

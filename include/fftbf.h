@@ -144,6 +144,22 @@ int fftbf_tied_set_window(fftbf_plan* plan, const double* hx, const double* hy, 
                           int trunc_y);
 
 /*
+ * Redundancy-stacked visibilities recovered from integrated FFT-beam intensities
+ * (Eq. inv_b2n-1). Per axis with pad >= 2n - 1 the beams are inverted onto the 2n - 1
+ * lags delta = -(n-1) .. n-1 (stored at index delta + n - 1):
+ *   V~_delta = (1/M) sum_A exp(+2 pi i delta A / M) P_A
+ * (the paper's n_ant / M factor is left to the caller, as in fftbf_execute); on an axis
+ * with pad < 2n - 1 the FFT beams do not determine every lag and the beam index is kept.
+ * V~_-delta = conj(V~_delta) and V~_0 is the total power.
+ *   beams_dev  device float [n_windows][nfreq][pad_x][pad_y] from fftbf_execute.
+ *   vis_dev    device complex FP32 (re, im interleaved) [n_windows][nfreq][Dx][Dy], with
+ *              Dx, Dy from fftbf_stacked_shape; overwritten.
+ */
+int fftbf_stacked_shape(const fftbf_plan* plan, int* dx, int* dy);
+int fftbf_stacked_visibilities(fftbf_plan* plan, const float* beams_dev, int64_t n_windows,
+                               float* vis_dev, void* stream);
+
+/*
  * The same pass as fftbf_execute followed by fftbf_tied_beams, on HOST buffers: the
  * voltages are copied to the device in window-sized chunks on a copy stream owned by
  * the plan, overlapped with the transform of the previous chunk on `stream`; the

@@ -7,4 +7,5 @@ from .fftbf_oracle import (  # noqa: F401
     beams, beams_from_field, beams_via_stacked, beams_via_visibilities, dft_phase,
     field_direct, field_separable, regrid_weights, stacked_visibilities, tied_direct,
     tied_regrid, tied_windowed_regrid, tied_windowed_visibility, truncate_nearest, unpack,
-    visibilities, window_lag_coeffs, windowed_regrid_weights)
+    visibilities, window_lag_coeffs, windowed_regrid_weights, stacked_from_beams,
+    stacked_ew_beams)

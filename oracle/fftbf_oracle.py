@@ -321,3 +321,48 @@ def truncate_nearest(weights, y, m, k) -> np.ndarray:
     rel = np.mod(np.arange(m, dtype=np.float64) - first[..., None], m)
     w[rel >= k] = 0.0
     return w
+
+
+# --- visibility-space products from FFT beams ------------------------------------------
+def _stack_axis(P, n, axis):
+    """Inverse DFT of FFT-beam intensities along `axis` onto lags delta = -(n-1) .. n-1
+    (stored at delta + n - 1): (1/M) sum_A exp(+2 pi i delta A / M) P_A (Eq. inv_b2n-1 in
+    this library's unnormalised convention). Needs M >= 2n - 1."""
+    m = P.shape[axis]
+    d = np.arange(-(n - 1), n)
+    E = np.exp(2j * np.pi * ((d[:, None] * np.arange(m)[None, :]) % m) / m) / m   # [2n-1, M]
+    P = np.moveaxis(np.asarray(P), axis, -1)
+    out = np.einsum("dA,...A->...d", E, P)
+    return np.moveaxis(out, -1, axis)
+
+
+def stacked_from_beams(P, nx, ny) -> np.ndarray:
+    """Redundancy-stacked visibilities recovered from FFT-beam intensities P[..., Mx, My].
+
+    On an axis with M >= 2n - 1 the beams are inverted onto lags (Eq. inv_b2n-1); on an
+    axis with M < 2n - 1 they do not determine every lag, and the FFT-beam index is kept.
+    Returns complex [..., Dx, Dy], D = 2n - 1 (lags) or M (beams) per axis."""
+    P = np.asarray(P, dtype=np.float64)
+    mx, my = P.shape[-2:]
+    out = P.astype(np.complex128)
+    if my >= 2 * ny - 1:
+        out = _stack_axis(out, ny, -1)
+    if mx >= 2 * nx - 1:
+        out = _stack_axis(out, nx, -2)
+    return out
+
+
+def stacked_ew_beams(x, w, mx, n_int) -> np.ndarray:
+    """N-S redundancy-stacked visibilities of each E-W FFT beam, formed from voltages:
+    sum_{t,p} sum_alpha Y_A(alpha + dy) Y_A(alpha)^*, Y_A(iy) = sum_ix E_x[A, ix] w x (the
+    partially stacked quantity when only the N-S axis is padded to 2n - 1). [J, F, Mx, 2ny-1]"""
+    x = np.asarray(x, dtype=np.complex128)
+    T, F, Pn, nx, ny = x.shape
+    ya = np.einsum("Ax,tfpxy->tfpAy", dft_phase(nx, mx), _weights(w, nx, ny) * x)
+    out = np.zeros((T // n_int, F, mx, 2 * ny - 1), dtype=np.complex128)
+    ya = ya.reshape(T // n_int, n_int, F, Pn, mx, ny)
+    for d in range(-(ny - 1), ny):
+        lo, hi = max(0, -d), min(ny, ny - d)
+        out[..., d + ny - 1] = np.einsum("jtfpAa,jtfpAa->jfA", ya[..., lo + d:hi + d],
+                                         np.conj(ya[..., lo:hi]))
+    return out

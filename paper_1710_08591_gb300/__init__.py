@@ -19,7 +19,8 @@ import threading
 import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
-           "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window",
+           "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window", "stacked_shape",
+           "stacked_visibilities",
            "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "Batch", "batch_create",
            "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
            "server_submit", "server_wait", "server_stats", "server_destroy"]
@@ -67,6 +68,10 @@ def lib() -> ctypes.CDLL:
             L.fftbf_tied_beams.argtypes = [vp, vp, c_i64, c_int, vp, vp, vp, vp]
             L.fftbf_tied_set_window.restype = c_int
             L.fftbf_tied_set_window.argtypes = [vp, vp, vp, c_int, c_int]
+            L.fftbf_stacked_shape.restype = c_int
+            L.fftbf_stacked_shape.argtypes = [vp, vp, vp]
+            L.fftbf_stacked_visibilities.restype = c_int
+            L.fftbf_stacked_visibilities.argtypes = [vp, vp, c_i64, vp, vp]
             L.fftbf_execute_host.restype = c_int
             L.fftbf_execute_host.argtypes = [vp, vp, c_i64, vp, c_int, vp, vp, vp, vp]
             L.fftbf_plan_sync.restype = c_int
@@ -227,6 +232,19 @@ def tied_set_window(plan: Plan, hx=None, hy=None, trunc_x: int = 0, trunc_y: int
     _check(lib().fftbf_tied_set_window(plan.handle, None if ax is None else ax.ctypes.data,
                                        None if ay is None else ay.ctypes.data, int(trunc_x),
                                        int(trunc_y)))
+
+
+def stacked_shape(plan: Plan) -> tuple[int, int]:
+    dx, dy = ctypes.c_int(), ctypes.c_int()
+    _check(lib().fftbf_stacked_shape(plan.handle, ctypes.byref(dx), ctypes.byref(dy)))
+    return dx.value, dy.value
+
+
+def stacked_visibilities(plan: Plan, beams, n_windows: int, vis, stream=None) -> None:
+    """Redundancy-stacked visibilities from FFT-beam intensities into `vis` (device,
+    complex64 [n_windows][nfreq][Dx][Dy], Dx, Dy = stacked_shape(plan))."""
+    _check(lib().fftbf_stacked_visibilities(plan.handle, _dptr(beams), int(n_windows), _dptr(vis),
+                                            _stream(stream)))
 
 
 def execute_host(plan: Plan, volts: np.ndarray, T: int, beams: np.ndarray, n_tied: int = 0,

@@ -1,0 +1,136 @@
+// Redundancy-stacked visibilities recovered from integrated FFT-beam intensities
+// (Eq. inv_b2n-1): per axis with pad M >= 2n - 1,
+//   V~_delta = (1/M) sum_A exp(+2 pi i delta A / M) P_A ,  |delta| < n,
+// the inverse of Eq. b2n-1 (the FFT beams hold the same information as V~_delta); on an
+// axis with M < 2n - 1 the FFT-beam index is kept. One CTA per (window, channel): the
+// N-S step reads the beam tile from shared memory and a table of exp(+2 pi i k / My), the
+// E-W step (if any) combines the Mx rows. FP32 sums of FP32 twiddles (from FP64).
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace fftbf {
+
+__global__ void __launch_bounds__(256) stacked_vis_kernel(const float* __restrict__ P,
+                                                          float2* __restrict__ out,
+                                                          const float2* __restrict__ tw_y,
+                                                          int64_t nitems, int nx, int ny,
+                                                          int mx, int my, int inv_x,
+                                                          int inv_y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int dx_n = inv_x ? 2 * nx - 1 : mx;
+  const int dy_n = inv_y ? 2 * ny - 1 : my;
+  float* ps = reinterpret_cast<float*>(smem);                       // [mx][my]
+  float2* tys = reinterpret_cast<float2*>(ps + ((mx * my + 1) & ~1)); // [my] exp(+2 pi i k/My)
+  float2* txs = tys + my;                                            // [mx] exp(+2 pi i k/Mx)
+  float2* q = txs + mx;                                              // [mx][dy_n]
+  for (int i = threadIdx.x; i < my; i += blockDim.x) {
+    const float2 t = tw_y[i];
+    tys[i] = make_float2(t.x, -t.y);
+  }
+  for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)i / (double)mx, &s, &c);
+    txs[i] = make_float2((float)c, (float)s);
+  }
+  const float iny = 1.0f / (float)my, inx = 1.0f / (float)mx;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    __syncthreads();
+    const float* src = P + item * (int64_t)(mx * my);
+    for (int i = threadIdx.x; i < mx * my; i += blockDim.x) ps[i] = src[i];
+    __syncthreads();
+    // N-S: q[A][d] = (1/My) sum_B exp(+2 pi i lag B / My) P[A][B]   (or q = P)
+    for (int o = threadIdx.x; o < mx * dy_n; o += blockDim.x) {
+      const int A = o / dy_n, d = o - A * dy_n;
+      float2 acc = make_float2(0.f, 0.f);
+      if (inv_y) {
+        const int lag = d - (ny - 1);
+        const unsigned lm = (unsigned)(((lag % my) + my) % my);
+        const float* row = ps + A * my;
+        unsigned idx = 0;
+        for (int B = 0; B < my; ++B) {
+          const float2 t = tys[idx];
+          acc.x = fmaf(t.x, row[B], acc.x);
+          acc.y = fmaf(t.y, row[B], acc.y);
+          idx += lm;
+          if (idx >= (unsigned)my) idx -= my;
+        }
+        acc.x *= iny;
+        acc.y *= iny;
+      } else {
+        acc.x = ps[A * my + d];
+      }
+      q[o] = acc;
+    }
+    __syncthreads();
+    // E-W: V[dx][d] = (1/Mx) sum_A exp(+2 pi i lag A / Mx) q[A][d]   (or V = q)
+    float2* dst = out + item * (int64_t)(dx_n * dy_n);
+    for (int o = threadIdx.x; o < dx_n * dy_n; o += blockDim.x) {
+      const int e = o / dy_n, d = o - e * dy_n;
+      float2 v;
+      if (inv_x) {
+        const int lag = e - (nx - 1);
+        const int lm = ((lag % mx) + mx) % mx;
+        v = make_float2(0.f, 0.f);
+        int idx = 0;
+        for (int A = 0; A < mx; ++A) {
+          const float2 t = txs[idx], z = q[A * dy_n + d];
+          v.x = fmaf(t.x, z.x, fmaf(-t.y, z.y, v.x));
+          v.y = fmaf(t.x, z.y, fmaf(t.y, z.x, v.y));
+          idx += lm;
+          if (idx >= mx) idx -= mx;
+        }
+        v.x *= inx;
+        v.y *= inx;
+      } else {
+        v = q[e * dy_n + d];
+      }
+      dst[o] = v;
+    }
+  }
+}
+
+}  // namespace fftbf
+
+using namespace fftbf;
+
+extern "C" {
+
+int fftbf_stacked_shape(const fftbf_plan* p, int* dx, int* dy) {
+  if (!p || !dx || !dy) return set_error(FFTBF_EINVAL, "null argument");
+  *dx = p->mx >= 2 * p->nx - 1 ? 2 * p->nx - 1 : p->mx;
+  *dy = p->my >= 2 * p->ny - 1 ? 2 * p->ny - 1 : p->my;
+  return FFTBF_OK;
+}
+
+int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_windows,
+                               float* vis_dev, void* stream) {
+  if (!p) return set_error(FFTBF_EINVAL, "null plan");
+  if (n_windows < 0) return set_error(FFTBF_EINVAL, "n_windows < 0");
+  if (n_windows == 0) return FFTBF_OK;
+  if (!beams_dev || !vis_dev) return set_error(FFTBF_EINVAL, "null buffer");
+  const int inv_x = p->mx >= 2 * p->nx - 1, inv_y = p->my >= 2 * p->ny - 1;
+  int dx = 0, dy = 0;
+  fftbf_stacked_shape(p, &dx, &dy);
+  const size_t smem = sizeof(float) * (((size_t)p->mx * p->my + 1) & ~(size_t)1) +
+                      sizeof(float2) * ((size_t)p->my + p->mx + (size_t)p->mx * dy);
+  if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "beam tile too large for the stacking kernel");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != p->device) cudaSetDevice(p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaFuncSetAttribute(stacked_vis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t items = n_windows * p->nfreq;
+  const int64_t grid = items < (int64_t)p->nsm * 4 ? items : (int64_t)p->nsm * 4;
+  if (e == cudaSuccess) {
+    stacked_vis_kernel<<<(unsigned)grid, 256, smem, st>>>(beams_dev, reinterpret_cast<float2*>(vis_dev),
+                                                          p->d_tw, items, p->nx, p->ny, p->mx,
+                                                          p->my, inv_x, inv_y);
+    e = cudaGetLastError();
+  }
+  if (prev != p->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_error(e, "fftbf_stacked_visibilities");
+  return FFTBF_OK;
+}
+
+}  // extern "C"
