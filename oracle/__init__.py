@@ -8,4 +8,4 @@ from .fftbf_oracle import (  # noqa: F401
     field_direct, field_separable, regrid_weights, stacked_visibilities, tied_direct,
     tied_regrid, tied_windowed_regrid, tied_windowed_visibility, truncate_nearest, unpack,
     visibilities, window_lag_coeffs, windowed_regrid_weights, stacked_from_beams,
-    stacked_ew_beams)
+    stacked_ew_beams, baseline_moi, regrid_weight_derivative, localise)
