@@ -380,6 +380,17 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         tied_forms["stacked_visibilities"] = {"ms": a0.elapsed_time(a1) / 3, "shape": [sdx, sdy]}
         del vis
+        # point-source localisation in every (window, channel) from the same FFT beams
+        loc = torch.empty((nwin, nfreq, 3), dtype=torch.float32, device=dev)
+        fb.localise(plan, beams, nwin, loc, 5, 10, stream)
+        torch.cuda.synchronize(dev)
+        a0.record(stream)
+        for _ in range(3):
+            fb.localise(plan, beams, nwin, loc, 5, 10, stream)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        tied_forms["localise"] = {"ms": a0.elapsed_time(a1) / 3, "n_iter": 5, "n_taps": 10}
+        del loc
 
     serving = None
     if not args.no_serving:

@@ -160,6 +160,22 @@ int fftbf_stacked_visibilities(fftbf_plan* plan, const float* beams_dev, int64_t
                                float* vis_dev, void* stream);
 
 /*
+ * Localisation of a point source from FFT-beam intensities (Section 4.3), one estimate
+ * per (window, channel): start at the strongest FFT beam, then on each axis with
+ * pad >= 2n - 1 (and n > 1) take n_iter Newton steps
+ *   y <- y + T'(y) n^2 / (4 pi^2 MOI T(y)),   MOI = sum_delta delta^2 (n - |delta|)
+ * with T, T' the pointed beam and its derivative regridded from the n_taps FFT beams
+ * nearest the estimate and the curvature taken at the maximum (Eq. baseline_MOI); an axis
+ * with pad < 2n - 1 keeps the beam position A / pad. The paper expects ~10 beams to hold a
+ * source's information; its uncertainty is sqrt(6) / (2 pi n SNR) in y.
+ *   beams_dev  device float [n_windows][nfreq][pad_x][pad_y] from fftbf_execute.
+ *   out_dev    device float [n_windows][nfreq][3]: y_x, y_y in [0, 1) (lattice units,
+ *              (d/lambda) sin(theta)) and the pointed beam T at the estimate.
+ */
+int fftbf_localise(fftbf_plan* plan, const float* beams_dev, int64_t n_windows, int n_iter,
+                   int n_taps, float* out_dev, void* stream);
+
+/*
  * The same pass as fftbf_execute followed by fftbf_tied_beams, on HOST buffers: the
  * voltages are copied to the device in window-sized chunks on a copy stream owned by
  * the plan, overlapped with the transform of the previous chunk on `stream`; the

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window", "stacked_shape",
-           "stacked_visibilities",
+           "stacked_visibilities", "localise",
            "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "Batch", "batch_create",
            "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
            "server_submit", "server_wait", "server_stats", "server_destroy"]
@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             L.fftbf_stacked_shape.argtypes = [vp, vp, vp]
             L.fftbf_stacked_visibilities.restype = c_int
             L.fftbf_stacked_visibilities.argtypes = [vp, vp, c_i64, vp, vp]
+            L.fftbf_localise.restype = c_int
+            L.fftbf_localise.argtypes = [vp, vp, c_i64, c_int, c_int, vp, vp]
             L.fftbf_execute_host.restype = c_int
             L.fftbf_execute_host.argtypes = [vp, vp, c_i64, vp, c_int, vp, vp, vp, vp]
             L.fftbf_plan_sync.restype = c_int
@@ -245,6 +247,13 @@ def stacked_visibilities(plan: Plan, beams, n_windows: int, vis, stream=None) ->
     complex64 [n_windows][nfreq][Dx][Dy], Dx, Dy = stacked_shape(plan))."""
     _check(lib().fftbf_stacked_visibilities(plan.handle, _dptr(beams), int(n_windows), _dptr(vis),
                                             _stream(stream)))
+
+
+def localise(plan: Plan, beams, n_windows: int, out, n_iter: int = 5, n_taps: int = 10,
+             stream=None) -> None:
+    """Point-source position per (window, channel) into `out` (device float [n_windows][nfreq][3])."""
+    _check(lib().fftbf_localise(plan.handle, _dptr(beams), int(n_windows), int(n_iter), int(n_taps),
+                                _dptr(out), _stream(stream)))
 
 
 def execute_host(plan: Plan, volts: np.ndarray, T: int, beams: np.ndarray, n_tied: int = 0,
