@@ -357,7 +357,12 @@ def run_ours(args, rank, world, local_rank):
                 fb.tied_beams(plan, beams, nwin, n_tied, u, v, tied, stream)
             a1.record(stream)
             torch.cuda.synchronize(dev)
-            tied_forms[name] = {"ms": a0.elapsed_time(a1) / 3}
+            tms = a0.elapsed_time(a1) / 3
+            # algorithmic flops: 2 per (tied beam, FFT beam used); E-W one FFT-beam column
+            # (pad_x < 2 nx - 1), N-S all pad_y beams or the truncated taps
+            k_ns = trunc if trunc else my
+            tfl = 2.0 * nwin * nfreq * n_tied * k_ns / (tms / 1e3) / 1e12
+            tied_forms[name] = {"ms": tms, "tflops": tfl, "frac_fp32_peak": tfl / FP32_PEAK_TFLOPS}
             if name == "window_gemm":
                 ref_dense = tied.clone()
             if name.endswith("tap"):
@@ -378,7 +383,11 @@ def run_ours(args, rank, world, local_rank):
             fb.stacked_visibilities(plan, beams, nwin, vis, stream)
         a1.record(stream)
         torch.cuda.synchronize(dev)
-        tied_forms["stacked_visibilities"] = {"ms": a0.elapsed_time(a1) / 3, "shape": [sdx, sdy]}
+        vms = a0.elapsed_time(a1) / 3
+        vbytes = nwin * nfreq * (mx * my * 4 + sdx * sdy * 8)          # beams in, visibilities out
+        tied_forms["stacked_visibilities"] = {
+            "ms": vms, "shape": [sdx, sdy], "gbs": vbytes / (vms / 1e3) / 1e9,
+            "frac_hbm": vbytes / (vms / 1e3) / 1e9 / peaks["hbm_gbs"]}
         del vis
         # point-source localisation in every (window, channel) from the same FFT beams
         loc = torch.empty((nwin, nfreq, 3), dtype=torch.float32, device=dev)
@@ -389,7 +398,11 @@ def run_ours(args, rank, world, local_rank):
             fb.localise(plan, beams, nwin, loc, 5, 10, stream)
         a1.record(stream)
         torch.cuda.synchronize(dev)
-        tied_forms["localise"] = {"ms": a0.elapsed_time(a1) / 3, "n_iter": 5, "n_taps": 10}
+        lms = a0.elapsed_time(a1) / 3
+        lbytes = nwin * nfreq * (mx * my * 4 + 12)
+        tied_forms["localise"] = {"ms": lms, "n_iter": 5, "n_taps": 10,
+                                  "gbs": lbytes / (lms / 1e3) / 1e9,
+                                  "frac_hbm": lbytes / (lms / 1e3) / 1e9 / peaks["hbm_gbs"]}
         del loc
 
     serving = None

@@ -169,8 +169,10 @@ int fftbf_stacked_visibilities(fftbf_plan* plan, const float* beams_dev, int64_t
  * with pad < 2n - 1 keeps the beam position A / pad. The paper expects ~10 beams to hold a
  * source's information; its uncertainty is sqrt(6) / (2 pi n SNR) in y.
  *   beams_dev  device float [n_windows][nfreq][pad_x][pad_y] from fftbf_execute.
+ *   n_iter >= 0; n_taps in 1 .. 64 (clipped to the pad of each axis), else FFTBF_EINVAL.
  *   out_dev    device float [n_windows][nfreq][3]: y_x, y_y in [0, 1) (lattice units,
  *              (d/lambda) sin(theta)) and the pointed beam T at the estimate.
+ * Weights are evaluated in FP32 from exactly reduced phases; T is summed in FP64.
  */
 int fftbf_localise(fftbf_plan* plan, const float* beams_dev, int64_t n_windows, int n_iter,
                    int n_taps, float* out_dev, void* stream);

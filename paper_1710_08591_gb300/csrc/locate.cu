@@ -7,8 +7,14 @@
 //   (Eq. bp_max_arbitrary and its derivative), the curvature taken at the maximum
 //   (Eq. baseline_MOI) and the sums truncated to the n_taps beams nearest the estimate;
 //   an axis with M < 2n - 1 keeps the beam position A/M.
-// Weights and sums in FP64 (the FFT beams are FP32); output (y_x, y_y, T(y)) with T
-// regridded from every FFT beam.
+// Output (y_x, y_y, T(y)) with T regridded from every FFT beam.
+//
+// Numerics: a position is kept as y M = ih + fr (integer ih, FP32 fraction fr in [0, 1)),
+// so that the distance to FFT beam B, e M = (ih - B) + fr, and the Dirichlet phase
+// (2n - 1) e mod 2 = [((2n - 1)(ih - B) mod 2M) + (2n - 1) fr] / M are formed from exact
+// integers plus one FP32 term; the weights w = sin((2n-1) pi e) / (M sin(pi e)) and their
+// derivative then come from FP32 sinpi/cospi, with a series near e = 0. The final sum of
+// the pointed beam is accumulated in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,53 +24,102 @@
 
 namespace fftbf {
 
-// Dirichlet regridding weight and its derivative at e = y - A/M (reduced to [-1/2, 1/2)).
-__device__ __forceinline__ void dirichlet_wd(int n, int M, double y, int A, double* w, double* dw) {
-  double e = y - (double)A / (double)M;
-  e -= rint(e);
-  const double L = 2.0 * n - 1.0;
-  if (fabs(e) < 1e-7) {
-    *w = L / M;
-    *dw = -(M_PI * M_PI * L * (L * L - 1.0) / (3.0 * M)) * e;
-    return;
+constexpr int kLocTaps = 64;          // most taps per axis
+constexpr int kLocWarps = 8;
+
+struct LocAxis {
+  int n, M, fit;
+  float invM, newton;                 // newton = n^2 / (4 pi^2 MOI)
+};
+
+// Dirichlet regridding weight of FFT beam B at the position (ih, fr), and its y-derivative.
+__device__ __forceinline__ void dir_weight(const LocAxis& ax, int ih, float fr, int B, float* w,
+                                           float* dw) {
+  const int M = ax.M, L = 2 * ax.n - 1;
+  int d = (ih - B) % M;                               // e M = d + fr, reduced to [-M/2, M/2)
+  if ((float)d + fr >= 0.5f * M) d -= M;
+  else if ((float)d + fr < -0.5f * M) d += M;
+  const float r = (float)d + fr;
+  const float e = r * ax.invM;
+  const int m2 = (int)(((long long)L * d) % (2LL * M));
+  float ph = ((float)m2 + (float)L * fr) * ax.invM;   // (2n - 1) e  (mod 2)
+  ph -= 2.f * rintf(0.5f * ph);
+  float sL, cL, s1, c1;
+  sincospif(ph, &sL, &cL);
+  sincospif(e, &s1, &c1);
+  const float Le = (float)L * e;
+  if (fabsf(Le) < 0.05f) {
+    // f(x) = sin(Lx)/sin(x) = L[1 + x^2 (1 - L^2)/6 + x^4 (7/360 - L^2/36 + L^4/120)] + ...
+    const float x = 3.14159265358979f * e, x2 = x * x, L2 = (float)L * (float)L;
+    const float c2 = (1.f - L2) * (1.f / 6.f);
+    const float c4 = 7.f / 360.f - L2 * (1.f / 36.f) + L2 * L2 * (1.f / 120.f);
+    *w = (float)L * (1.f + x2 * (c2 + x2 * c4)) * ax.invM;
+    *dw = 3.14159265358979f * (float)L * x * (2.f * c2 + 4.f * c4 * x2) * ax.invM;
+  } else {
+    *w = sL / (s1 * (float)M);
+    *dw = 3.14159265358979f * ax.invM * ((float)L * cL * s1 - sL * c1) / (s1 * s1);
   }
-  double sL, cL, s1, c1;
-  sincospi(L * e, &sL, &cL);
-  sincospi(e, &s1, &c1);
-  *w = sL / (s1 * M);
-  *dw = (M_PI / M) * (L * cL * s1 - sL * c1) / (s1 * s1);
 }
 
-__device__ __forceinline__ int first_near(int M, double y, int k) {
-  long long f0 = (long long)floor(y * (double)M - 0.5 * (k - 1) + 0.5);
-  f0 %= M;
-  if (f0 < 0) f0 += M;
-  return (int)f0;
+// first of the k taps nearest y M = ih + fr: floor(y M - (k - 1)/2 + 1/2), mod M
+__device__ __forceinline__ int first_tap(int M, int ih, float fr, int k) {
+  int f = ih + (int)floorf(fr + 0.5f - 0.5f * (float)(k - 1));
+  f %= M;
+  return f < 0 ? f + M : f;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__global__ void __launch_bounds__(256) localise_kernel(const float* __restrict__ P,
-                                                       float* __restrict__ out, int64_t items,
-                                                       int nx, int ny, int mx, int my,
-                                                       int fit_x, int fit_y, int n_iter,
-                                                       int taps_x, int taps_y, double moi_x,
-                                                       double moi_y) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < items;
-       item += warps) {
-    const float* tile = P + item * (int64_t)(mx * my);
+// advance a position by dy (in units of y) and renormalise fr into [0, 1), ih into [0, M)
+__device__ __forceinline__ void move(int M, int* ih, float* fr, float dyM) {
+  float f = *fr + dyM;
+  const float k = floorf(f);
+  f -= k;
+  if (f >= 1.f) f = 0.f;                               // rounding of f - k at the top end
+  int i = (*ih + (int)k) % M;
+  *ih = i < 0 ? i + M : i;
+  *fr = f;
+}
+
+__global__ void __launch_bounds__(32 * kLocWarps) localise_kernel(
+    const float* __restrict__ P, float* __restrict__ out, int64_t items, LocAxis axx,
+    LocAxis axy, int n_iter, int taps_x, int taps_y, int vec4) {
+  __shared__ float sw[kLocWarps][4][kLocTaps];         // wx, dwx, wy, dwy of the taps
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* wx = sw[wib][0];
+  float* dwx = sw[wib][1];
+  float* wy = sw[wib][2];
+  float* dwy = sw[wib][3];
+  const int mx = axx.M, my = axy.M, nel = mx * my;
+  const int64_t warps = (int64_t)gridDim.x * kLocWarps;
+  for (int64_t item = (int64_t)blockIdx.x * kLocWarps + wib; item < items; item += warps) {
+    const float* tile = P + item * (int64_t)nel;
     // first maximum
     float best = -INFINITY;
     int bi = 0x7fffffff;
-    for (int i = lane; i < mx * my; i += 32) {
-      const float v = tile[i];
-      if (v > best) { best = v; bi = i; }
+    if (vec4) {
+      const float4* t4 = reinterpret_cast<const float4*>(tile);
+      for (int i = lane; i < (nel >> 2); i += 32) {
+        const float4 v = t4[i];
+        if (v.x > best) { best = v.x; bi = 4 * i; }
+        if (v.y > best) { best = v.y; bi = 4 * i + 1; }
+        if (v.z > best) { best = v.z; bi = 4 * i + 2; }
+        if (v.w > best) { best = v.w; bi = 4 * i + 3; }
+      }
+    } else {
+      for (int i = lane; i < nel; i += 32) {
+        const float v = tile[i];
+        if (v > best) { best = v; bi = i; }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -72,45 +127,75 @@ __global__ void __launch_bounds__(256) localise_kernel(const float* __restrict__
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    if (bi >= mx * my) bi = 0;                      // a tile with no ordered value (NaN)
+    if (bi >= nel) bi = 0;                             // a tile with no ordered value (NaN)
     const int a0 = bi / my, b0 = bi - (bi / my) * my;
-    double yx = (double)a0 / mx, yy = (double)b0 / my;
-    const int kx = fit_x ? taps_x : 1, ky = fit_y ? taps_y : 1;
+    int ihx = a0, ihy = b0;
+    float frx = 0.f, fry = 0.f;
+    const int kx = axx.fit ? taps_x : 1, ky = axy.fit ? taps_y : 1;
     for (int it = 0; it < n_iter; ++it) {
-      const int fx = fit_x ? first_near(mx, yx, kx) : a0;
-      const int fy = fit_y ? first_near(my, yy, ky) : b0;
-      double T = 0.0, Dx = 0.0, Dy = 0.0;
+      const int fx = axx.fit ? first_tap(mx, ihx, frx, kx) : a0;
+      const int fy = axy.fit ? first_tap(my, ihy, fry, ky) : b0;
+      for (int t = lane; t < kx; t += 32) {
+        float w = 1.f, d = 0.f;
+        if (axx.fit) dir_weight(axx, ihx, frx, (fx + t) % mx, &w, &d);
+        wx[t] = w;
+        dwx[t] = d;
+      }
+      for (int t = lane; t < ky; t += 32) {
+        float w = 1.f, d = 0.f;
+        if (axy.fit) dir_weight(axy, ihy, fry, (fy + t) % my, &w, &d);
+        wy[t] = w;
+        dwy[t] = d;
+      }
+      __syncwarp();
+      float T = 0.f, Dx = 0.f, Dy = 0.f;
       for (int q = lane; q < kx * ky; q += 32) {
         const int tx = q / ky, ty = q - (q / ky) * ky;
-        const int A = (fx + tx) % mx, B = (fy + ty) % my;
-        double wx = 1.0, dwx = 0.0, wy = 1.0, dwy = 0.0;
-        if (fit_x) dirichlet_wd(nx, mx, yx, A, &wx, &dwx);
-        if (fit_y) dirichlet_wd(ny, my, yy, B, &wy, &dwy);
-        const double p = (double)tile[A * my + B];
-        T += wx * wy * p;
-        Dx += dwx * wy * p;
-        Dy += wx * dwy * p;
+        const float p = tile[((fx + tx) % mx) * my + (fy + ty) % my];
+        T = fmaf(wx[tx] * wy[ty], p, T);
+        Dx = fmaf(dwx[tx] * wy[ty], p, Dx);
+        Dy = fmaf(wx[tx] * dwy[ty], p, Dy);
       }
-      T = warp_sum(T);
-      Dx = warp_sum(Dx);
-      Dy = warp_sum(Dy);
-      const double fourpi2 = 4.0 * M_PI * M_PI;
-      if (fit_x) yx += Dx * (double)nx * nx / (fourpi2 * moi_x * T);
-      if (fit_y) yy += Dy * (double)ny * ny / (fourpi2 * moi_y * T);
+      T = warp_sum_f(T);
+      Dx = warp_sum_f(Dx);
+      Dy = warp_sum_f(Dy);
+      __syncwarp();
+      if (axx.fit) move(mx, &ihx, &frx, Dx * axx.newton / T * (float)mx);
+      if (axy.fit) move(my, &ihy, &fry, Dy * axy.newton / T * (float)my);
     }
-    // the pointed beam at the estimate, from every FFT beam
+    // the pointed beam at the estimate, from every FFT beam: sum_B w^B sum_A w^A P[A, B]
     double T = 0.0;
-    for (int i = lane; i < mx * my; i += 32) {
-      const int A = i / my, B = i - (i / my) * my;
-      double wx = (A == a0) ? 1.0 : 0.0, wy = (B == b0) ? 1.0 : 0.0, d;
-      if (fit_x) dirichlet_wd(nx, mx, yx, A, &wx, &d);
-      if (fit_y) dirichlet_wd(ny, my, yy, B, &wy, &d);
-      T += wx * wy * (double)tile[i];
+    if (axx.fit) {
+      for (int c = 0; c < mx; c += kLocTaps) {
+        for (int t = lane; t < kLocTaps && c + t < mx; t += 32) {
+          float w, d;
+          dir_weight(axx, ihx, frx, c + t, &w, &d);
+          wx[t] = w;
+        }
+        __syncwarp();
+        const int na = mx - c < kLocTaps ? mx - c : kLocTaps;
+        for (int B = lane; B < my; B += 32) {
+          float wB = 1.f, d;
+          if (axy.fit) dir_weight(axy, ihy, fry, B, &wB, &d);
+          else if (B != b0) continue;
+          float s = 0.f;
+          for (int A = 0; A < na; ++A) s = fmaf(wx[A], tile[(c + A) * my + B], s);
+          T += (double)(wB * s);
+        }
+        __syncwarp();
+      }
+    } else {
+      for (int B = lane; B < my; B += 32) {
+        float wB = 1.f, d;
+        if (axy.fit) dir_weight(axy, ihy, fry, B, &wB, &d);
+        else if (B != b0) continue;
+        T += (double)(wB * tile[a0 * my + B]);
+      }
     }
-    T = warp_sum(T);
+    T = warp_sum_d(T);
     if (lane == 0) {
-      out[3 * item] = (float)(yx - floor(yx));
-      out[3 * item + 1] = (float)(yy - floor(yy));
+      out[3 * item] = (float)(((double)ihx + (double)frx) / (double)mx);
+      out[3 * item + 1] = (float)(((double)ihy + (double)fry) / (double)my);
       out[3 * item + 2] = (float)T;
     }
   }
@@ -123,25 +208,32 @@ using namespace fftbf;
 extern "C" int fftbf_localise(fftbf_plan* p, const float* beams_dev, int64_t n_windows,
                               int n_iter, int n_taps, float* out_dev, void* stream) {
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
-  if (n_windows < 0 || n_iter < 0 || n_taps < 1)
-    return set_error(FFTBF_EINVAL, "need n_windows >= 0, n_iter >= 0, n_taps >= 1");
+  if (n_windows < 0 || n_iter < 0 || n_taps < 1 || n_taps > kLocTaps)
+    return set_error(FFTBF_EINVAL, "need n_windows >= 0, n_iter >= 0, 1 <= n_taps <= %d",
+                     kLocTaps);
   if (n_windows == 0) return FFTBF_OK;
   if (!beams_dev || !out_dev) return set_error(FFTBF_EINVAL, "null buffer");
-  const int fit_x = p->mx >= 2 * p->nx - 1 && p->nx > 1;
-  const int fit_y = p->my >= 2 * p->ny - 1 && p->ny > 1;
-  auto moi = [](int n) {
-    double s = 0.0;
-    for (int d = -(n - 1); d < n; ++d) s += (double)d * d * (n - (d < 0 ? -d : d));
-    return s;
+  auto axis = [](int n, int M) {
+    LocAxis a;
+    a.n = n;
+    a.M = M;
+    a.fit = M >= 2 * n - 1 && n > 1;
+    a.invM = (float)(1.0 / M);
+    double moi = 0.0;
+    for (int d = -(n - 1); d < n; ++d) moi += (double)d * d * (n - (d < 0 ? -d : d));
+    a.newton = moi > 0.0 ? (float)((double)n * n / (4.0 * M_PI * M_PI * moi)) : 0.f;
+    return a;
   };
+  const LocAxis ax = axis(p->nx, p->mx), ay = axis(p->ny, p->my);
+  const int vec4 = ((p->mx * p->my) % 4 == 0) && ((reinterpret_cast<uintptr_t>(beams_dev) & 15) == 0);
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != p->device) cudaSetDevice(p->device);
   const int64_t items = n_windows * p->nfreq;
-  const int64_t blocks = std::min<int64_t>((items + 7) / 8, (int64_t)p->nsm * 16);
-  localise_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-      beams_dev, out_dev, items, p->nx, p->ny, p->mx, p->my, fit_x, fit_y, n_iter,
-      std::min(n_taps, p->mx), std::min(n_taps, p->my), moi(p->nx), moi(p->ny));
+  const int64_t blocks = std::min<int64_t>((items + kLocWarps - 1) / kLocWarps, (int64_t)p->nsm * 8);
+  localise_kernel<<<(unsigned)blocks, 32 * kLocWarps, 0, static_cast<cudaStream_t>(stream)>>>(
+      beams_dev, out_dev, items, ax, ay, n_iter, std::min(n_taps, p->mx), std::min(n_taps, p->my),
+      vec4);
   const cudaError_t e = cudaGetLastError();
   if (prev != p->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_error(e, "fftbf_localise");

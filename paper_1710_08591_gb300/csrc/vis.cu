@@ -2,7 +2,7 @@
 // (Eq. inv_b2n-1): per axis with pad M >= 2n - 1,
 //   V~_delta = (1/M) sum_A exp(+2 pi i delta A / M) P_A ,  |delta| < n,
 // the inverse of Eq. b2n-1 (the FFT beams hold the same information as V~_delta); on an
-// axis with M < 2n - 1 the FFT-beam index is kept. One CTA per (window, channel): the
+// axis with M < 2n - 1 the FFT-beam index is kept. Direct route, one CTA per (window, channel): the
 // N-S step reads the beam tile from shared memory and a table of exp(+2 pi i k / My), the
 // E-W step (if any) combines the Mx rows. FP32 sums of FP32 twiddles (from FP64).
 #include <cuda_runtime.h>
@@ -90,6 +90,95 @@ __global__ void __launch_bounds__(256) stacked_vis_kernel(const float* __restric
   }
 }
 
+// The same N-S inversion by FFT when My is a power of two: two beam rows a, b share one
+// complex transform z = P_a + i P_b, Z[k] = sum_B z_B exp(+2 pi i k B / My) (radix-2
+// Stockham in shared memory), and the rows separate by Hermitian symmetry,
+//   X_a[k] = (Z[k] + conj Z[My-k]) / 2,   X_b[k] = (Z[k] - conj Z[My-k]) / 2i,
+// with V~_delta = X[delta] / My for delta >= 0 and conj(X[-delta]) / My below. The E-W step
+// (when Mx >= 2nx - 1) is the direct one above.
+__global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __restrict__ P,
+                                                              float2* __restrict__ out,
+                                                              const float2* __restrict__ tw_y,
+                                                              int64_t nitems, int nx, int ny,
+                                                              int mx, int my, int inv_x) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int half = my >> 1, dy_n = 2 * ny - 1, dx_n = inv_x ? 2 * nx - 1 : mx;
+  float2* twp = reinterpret_cast<float2*>(smem);   // [My/2] exp(+2 pi i k / My)
+  float2* buf0 = twp + half;                       // [My]
+  float2* buf1 = buf0 + my;                        // [My]
+  float2* q = buf1 + my;                           // [Mx][dy_n] when inverting E-W
+  float2* txs = q + (inv_x ? mx * dy_n : 0);       // [Mx] exp(+2 pi i k / Mx)
+  for (int i = threadIdx.x; i < half; i += blockDim.x) {
+    const float2 t = tw_y[i];
+    twp[i] = make_float2(t.x, -t.y);
+  }
+  if (inv_x)
+    for (int i = threadIdx.x; i < mx; i += blockDim.x) {
+      double s, c;
+      sincospi(2.0 * (double)i / (double)mx, &s, &c);
+      txs[i] = make_float2((float)c, (float)s);
+    }
+  const float iny = 1.0f / (float)my, inx = 1.0f / (float)mx;
+  for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const float* tile = P + item * (int64_t)(mx * my);
+    float2* dst = out + item * (int64_t)(dx_n * dy_n);
+    for (int r = 0; r < mx; r += 2) {
+      __syncthreads();
+      const float* ra = tile + r * my;
+      const bool two = r + 1 < mx;
+      for (int B = threadIdx.x; B < my; B += blockDim.x)
+        buf0[B] = make_float2(ra[B], two ? ra[my + B] : 0.f);
+      __syncthreads();
+      float2* src = buf0;
+      float2* dsb = buf1;
+      for (int ns = 1; ns < my; ns <<= 1) {
+        for (int j = threadIdx.x; j < half; j += blockDim.x) {
+          const int k = j & (ns - 1);
+          const float2 w = twp[k * (half / ns)];
+          const float2 a = src[j], b0 = src[j + half];
+          const float2 b = make_float2(b0.x * w.x - b0.y * w.y, b0.x * w.y + b0.y * w.x);
+          const int d = ((j - k) << 1) + k;
+          dsb[d] = make_float2(a.x + b.x, a.y + b.y);
+          dsb[d + ns] = make_float2(a.x - b.x, a.y - b.y);
+        }
+        __syncthreads();
+        float2* t = src; src = dsb; dsb = t;
+      }
+      for (int o = threadIdx.x; o < 2 * dy_n; o += blockDim.x) {
+        const int row = o >= dy_n, d = o - row * dy_n;
+        if (r + row >= mx) continue;
+        const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
+        const float2 zk = src[k], zm = src[(my - k) & (my - 1)];
+        float2 x = row == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
+                            : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        if (lag < 0) x.y = -x.y;
+        x.x *= iny;
+        x.y *= iny;
+        if (inv_x) q[(r + row) * dy_n + d] = x;
+        else dst[(r + row) * dy_n + d] = x;
+      }
+    }
+    if (inv_x) {
+      __syncthreads();
+      for (int o = threadIdx.x; o < dx_n * dy_n; o += blockDim.x) {
+        const int e = o / dy_n, d = o - e * dy_n;
+        const int lag = e - (nx - 1);
+        const int lm = ((lag % mx) + mx) % mx;
+        float2 v = make_float2(0.f, 0.f);
+        int idx = 0;
+        for (int A = 0; A < mx; ++A) {
+          const float2 t = txs[idx], z = q[A * dy_n + d];
+          v.x = fmaf(t.x, z.x, fmaf(-t.y, z.y, v.x));
+          v.y = fmaf(t.x, z.y, fmaf(t.y, z.x, v.y));
+          idx += lm;
+          if (idx >= mx) idx -= mx;
+        }
+        dst[o] = make_float2(v.x * inx, v.y * inx);
+      }
+    }
+  }
+}
+
 }  // namespace fftbf
 
 using namespace fftbf;
@@ -112,21 +201,44 @@ int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_
   const int inv_x = p->mx >= 2 * p->nx - 1, inv_y = p->my >= 2 * p->ny - 1;
   int dx = 0, dy = 0;
   fftbf_stacked_shape(p, &dx, &dy);
+  // FFT route: N-S invertible and My a power of two (>= 2)
+  const bool fft = inv_y && p->my >= 2 && (p->my & (p->my - 1)) == 0;
+  const size_t smem_fft = sizeof(float2) * ((size_t)p->my / 2 + 2 * (size_t)p->my +
+                                            (inv_x ? (size_t)p->mx * dy + p->mx : 0));
   const size_t smem = sizeof(float) * (((size_t)p->mx * p->my + 1) & ~(size_t)1) +
                       sizeof(float2) * ((size_t)p->my + p->mx + (size_t)p->mx * dy);
-  if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "beam tile too large for the stacking kernel");
+  const bool use_fft = fft && smem_fft <= 200 * 1024;
+  if (!use_fft && smem > 200 * 1024)
+    return set_error(FFTBF_EUNSUPPORTED, "beam tile too large for the stacking kernel");
   int prev = 0;
   cudaGetDevice(&prev);
   if (prev != p->device) cudaSetDevice(p->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaFuncSetAttribute(stacked_vis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t items = n_windows * p->nfreq;
-  const int64_t grid = items < (int64_t)p->nsm * 4 ? items : (int64_t)p->nsm * 4;
-  if (e == cudaSuccess) {
-    stacked_vis_kernel<<<(unsigned)grid, 256, smem, st>>>(beams_dev, reinterpret_cast<float2*>(vis_dev),
-                                                          p->d_tw, items, p->nx, p->ny, p->mx,
-                                                          p->my, inv_x, inv_y);
-    e = cudaGetLastError();
+  cudaError_t e;
+  if (use_fft) {
+    e = cudaFuncSetAttribute(stacked_vis_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_fft);
+    // resident CTAs per SM from shared memory (256 threads each, at most 8 by threads)
+    int per_sm = (int)((200 * 1024) / (smem_fft + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    const int64_t cap = (int64_t)p->nsm * per_sm;
+    const int64_t grid = items < cap ? items : cap;
+    if (e == cudaSuccess) {
+      stacked_vis_fft_kernel<<<(unsigned)grid, 256, smem_fft, st>>>(
+          beams_dev, reinterpret_cast<float2*>(vis_dev), p->d_tw, items, p->nx, p->ny, p->mx,
+          p->my, inv_x);
+      e = cudaGetLastError();
+    }
+  } else {
+    e = cudaFuncSetAttribute(stacked_vis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t grid = items < (int64_t)p->nsm * 4 ? items : (int64_t)p->nsm * 4;
+    if (e == cudaSuccess) {
+      stacked_vis_kernel<<<(unsigned)grid, 256, smem, st>>>(beams_dev, reinterpret_cast<float2*>(vis_dev),
+                                                            p->d_tw, items, p->nx, p->ny, p->mx,
+                                                            p->my, inv_x, inv_y);
+      e = cudaGetLastError();
+    }
   }
   if (prev != p->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return cuda_error(e, "fftbf_stacked_visibilities");
