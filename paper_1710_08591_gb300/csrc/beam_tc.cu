@@ -13,8 +13,12 @@
 //     square it and add it to 16 register accumulators (Eq. bf), so integration over time
 //     and polarisation needs no cross-lane reduction.
 // Operands are FP16 or BF16 (the 4-bit inputs are exact in both), accumulation is FP32.
-// Unpacking, apodisation and the 4-point E-W DFT run in FP32 on the CUDA cores, as in the
-// FP32 form, and are rounded to 16 bits once (times a plan scale that keeps FP16 finite).
+// BF16 form: unpacking, apodisation and the 4-point E-W DFT run in FP32 on the CUDA cores,
+// as in the FP32 form, and are rounded to 16 bits once (times a plan scale). FP16 form:
+// the same steps in packed-half arithmetic (nibbles decoded exactly into half2 through
+// the mantissa of 1024, weight x scale pre-rounded to FP16, the E-W butterflies in half2)
+// and the twiddle between the stages as a half2 complex multiply; this roughly halves the
+// CUDA-core instructions per snapshot at about 1.3x the FP16 rounding error.
 // A CTA (4 warps, 128 TMEM columns) processes the two polarisations of one time sample
 // (two snapshots) per iteration; four CTAs share an SM's 512 TMEM columns. Every wait on
 // the tensor core is bounded by device time; on timeout the kernel records an error word
@@ -49,6 +53,66 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
   }
+}
+
+// ---- packed-half helpers of the FP16 form ------------------------------------------------
+__device__ __forceinline__ __half2 u2h(uint32_t v) { return *reinterpret_cast<__half2*>(&v); }
+__device__ __forceinline__ uint32_t h2u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+// Byte k of `w` (bits 7..4 real, 3..0 imaginary, two's complement) as the exact half2
+// (16 re, im): the nibbles are placed in the mantissas of 1024 (0x6400), the real one four
+// bits up, with their sign bits flipped, which gives (1152 + 16 re, 1032 + im).
+__device__ __forceinline__ __half2 unpack16(uint32_t w, int k) {
+  const uint32_t t = __byte_perm(w, 0u, 0x4040u | (uint32_t)k | ((uint32_t)k << 8));
+  const uint32_t u = (t & 0x000F00F0u) ^ 0x64086480u;
+  return __hsub2(u2h(u), u2h(0x64086480u));           // (1152, 1032) as half2
+}
+
+// 4-point forward DFT of packed-half complex values, v[A] <- sum_ix v[ix] (-i)^(A ix).
+__device__ __forceinline__ void dft4_h2(__half2* v) {
+  const __half2 a = __hadd2(v[0], v[2]), b = __hsub2(v[0], v[2]);
+  const __half2 c = __hadd2(v[1], v[3]), d = __hsub2(v[1], v[3]);
+  const __half2 dsw = __lowhigh2highlow(d);            // (d.im, d.re)
+  v[0] = __hadd2(a, c);
+  v[2] = __hsub2(a, c);
+  v[1] = __hfma2(dsw, u2h(0xBC003C00u), b);            // b - i d: (1, -1)
+  v[3] = __hfma2(dsw, u2h(0x3C00BC00u), b);            // b + i d: (-1, 1)
+}
+
+// FP16 form, stage-1 operand of one snapshot pair: A1[(s, A, n2)][(n1, c)] = scale x the
+// E-W DFT of w x over the feeds iy = n2 + 16 n1. Thread (s, j, n2) forms n1 = 4j .. 4j + 3,
+// so each E-W beam A is one 16-byte core-matrix row (one store), lanes run over n2 (the
+// stores of a warp fill all banks) and the weights [ix][iy] are read 128 bytes at a time.
+// Feeds iy >= ny and a missing second snapshot (odd n_int * npol) give zeros.
+__device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned char* raw,
+                                              const uint2* w16, int nant, int ny, int tid,
+                                              bool snap1_ok, int lbo, int sbo) {
+  const int s = tid >> 6, j = (tid >> 4) & 3, n2 = tid & 15;
+  const bool sok = s == 0 || snap1_ok;
+  const unsigned char* rs = raw + s * nant;
+  uint32_t o[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int iy = n2 + 64 * j + 16 * kk;
+    __half2 z[4];
+#pragma unroll
+    for (int A = 0; A < 4; ++A) z[A] = u2h(0u);
+    if (sok && iy < ny) {
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix) {
+        const __half2 x = unpack16((uint32_t)rs[ix * ny + iy], 0);
+        const uint2 wv = w16[ix * ny + iy];
+        z[ix] = __hfma2(__high2half2(x), u2h(wv.y), __hmul2(__low2half2(x), u2h(wv.x)));
+      }
+      dft4_h2(z);
+    }
+#pragma unroll
+    for (int A = 0; A < 4; ++A) o[A][kk] = h2u(z[A]);
+  }
+#pragma unroll
+  for (int A = 0; A < 4; ++A)
+    *reinterpret_cast<uint4*>(a1 + tc::kmajor_off(s * 64 + A * 16 + n2, 8 * j, lbo, sbo)) =
+        make_uint4(o[A][0], o[A][1], o[A][2], o[A][3]);
 }
 
 struct TcSmem {
@@ -118,8 +182,30 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
   }
   load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
   load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
-  for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
-  for (int i = tid; i < nant; i += tcl::NT) wsm[i] = a.w[i];
+  // FP16 form: packed-half input stage when the E-W axis is a plain 4-point DFT over
+  // groups of four N-S feeds (4-byte words), and packed-half twiddles between the stages.
+  const bool fast16 = !BF16 && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny;
+  if constexpr (!BF16) {
+    uint2* tw16 = reinterpret_cast<uint2*>(twsm);      // [k1][n2] {(c, d), (-d, c)}
+    for (int i = tid; i < 512; i += tcl::NT) {
+      const float2 t = a.tw[(i >> 4) * (i & 15)];
+      tw16[i] = make_uint2(pack2<false>(t.x, t.y), pack2<false>(-t.y, t.x));
+    }
+  } else {
+    for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
+  }
+  if (fast16) {
+    // per feed {scale w / 16, scale i w}: (16 re, im) -> scale (re + i im) w
+    uint2* w16 = reinterpret_cast<uint2*>(wsm);
+    const float sc = ta.scale;
+    for (int i = tid; i < nant; i += tcl::NT) {
+      const float2 w = a.w[i];
+      w16[i] = make_uint2(pack2<false>(w.x * sc * 0.0625f, w.y * sc * 0.0625f),
+                          pack2<false>(-w.y * sc, w.x * sc));
+    }
+  } else {
+    for (int i = tid; i < nant; i += tcl::NT) wsm[i] = a.w[i];
+  }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -179,6 +265,10 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
 
     // ---- unpack x weight, E-W DFT, scale, round: stage-1 operand A1[(s,A,n2)][(n1,c)]
     const unsigned char* raw = raw0 + cur * rawsz;
+    if (fast16) {
+      input_stage16(a1, raw, reinterpret_cast<const uint2*>(wsm), nant, a.ny, tid,
+                    2 * it + 1 < nsnap, tcl::A1_LBO, tcl::A1_SBO);
+    } else
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = tid + q * tcl::NT;
@@ -235,10 +325,17 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int k1 = 16 * half + j;
-          const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-          const float2 y = cmul(x, twsm[k1 * 16 + n2]);   // lanes: consecutive n2
-          *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
-              pack2<BF16>(y.x, y.y);
+          uint32_t yv;
+          if constexpr (!BF16) {
+            const uint2 t = reinterpret_cast<const uint2*>(twsm)[k1 * 16 + n2];
+            const __half2 h = __floats2half2_rn(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            yv = h2u(__hfma2(__high2half2(h), u2h(t.y), __hmul2(__low2half2(h), u2h(t.x))));
+          } else {
+            const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            const float2 y = cmul(x, twsm[k1 * 16 + n2]);   // lanes: consecutive n2
+            yv = pack2<BF16>(y.x, y.y);
+          }
+          *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) = yv;
         }
       }
     }
@@ -377,8 +474,27 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
   }
   load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcp::NT);
   load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcp::NT);
-  for (int i = tid; i < 512; i += tcp::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
-  for (int i = tid; i < nant; i += tcp::NT) wsm[i] = a.w[i];
+  const bool fast16 = !BF16 && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny;
+  if constexpr (!BF16) {
+    uint2* tw16 = reinterpret_cast<uint2*>(twsm);      // [k1][n2] {(c, d), (-d, c)}
+    for (int i = tid; i < 512; i += tcp::NT) {
+      const float2 t = a.tw[(i >> 4) * (i & 15)];
+      tw16[i] = make_uint2(pack2<false>(t.x, t.y), pack2<false>(-t.y, t.x));
+    }
+  } else {
+    for (int i = tid; i < 512; i += tcp::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
+  }
+  if (fast16) {
+    uint2* w16 = reinterpret_cast<uint2*>(wsm);
+    const float sc = ta.scale;
+    for (int i = tid; i < nant; i += tcp::NT) {
+      const float2 w = a.w[i];
+      w16[i] = make_uint2(pack2<false>(w.x * sc * 0.0625f, w.y * sc * 0.0625f),
+                          pack2<false>(-w.y * sc, w.x * sc));
+    }
+  } else {
+    for (int i = tid; i < nant; i += tcp::NT) wsm[i] = a.w[i];
+  }
   for (int i = tid; i < 256; i += tcp::NT) lut[i] = unpack_byte((unsigned)i);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -436,6 +552,10 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
       if (!*pvote) { if (tid == 0) fail(); break; }
       const unsigned char* raw = raw0 + (p & 1) * rawsz;
       unsigned char* a1b = a1 + b * tcl::A1_BYTES;
+      if (fast16) {
+        input_stage16(a1b, raw, reinterpret_cast<const uint2*>(wsm), nant, a.ny, tid,
+                      2 * it + 1 < nsnap, tcl::A1_LBO, tcl::A1_SBO);
+      } else
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = tid + q * 128;
@@ -502,10 +622,17 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int k1 = 16 * half + j;
-            const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-            const float2 y = cmul(x, twsm[k1 * 16 + n2]);
-            *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
-                pack2<BF16>(y.x, y.y);
+            uint32_t yv;
+            if constexpr (!BF16) {
+              const uint2 t = reinterpret_cast<const uint2*>(twsm)[k1 * 16 + n2];
+              const __half2 h = __floats2half2_rn(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+              yv = h2u(__hfma2(__high2half2(h), u2h(t.y), __hmul2(__low2half2(h), u2h(t.x))));
+            } else {
+              const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+              const float2 y = cmul(x, twsm[k1 * 16 + n2]);
+              yv = pack2<BF16>(y.x, y.y);
+            }
+            *reinterpret_cast<uint32_t*>(a2s + tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) = yv;
           }
         }
         tc::fence_before_sync();
