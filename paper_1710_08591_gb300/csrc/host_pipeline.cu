@@ -15,10 +15,10 @@ void host_pipe_free(HostPipe& hp) {
       cudaStreamSynchronize(hp.copy_extra[k]);
       cudaStreamDestroy(hp.copy_extra[k]);
     }
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < HostPipe::kStages; ++b)
       if (hp.copied_extra[b][k]) cudaEventDestroy(hp.copied_extra[b][k]);
   }
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < HostPipe::kStages; ++b) {
     if (hp.copied[b]) cudaEventDestroy(hp.copied[b]);
     if (hp.freed[b]) cudaEventDestroy(hp.freed[b]);
     cudaFree(hp.stage[b]);
@@ -69,13 +69,13 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
   HostPipe& hp = p->pipe;
   if (!hp.copy) {
     FFTBF_CUDA_TRY(cudaStreamCreateWithFlags(&hp.copy, cudaStreamNonBlocking));
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < HostPipe::kStages; ++b) {
       FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.copied[b], cudaEventDisableTiming));
       FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.freed[b], cudaEventDisableTiming));
     }
     for (int k = 0; k < HostPipe::kCopyStreams - 1; ++k) {
       FFTBF_CUDA_TRY(cudaStreamCreateWithFlags(&hp.copy_extra[k], cudaStreamNonBlocking));
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < HostPipe::kStages; ++b)
         FFTBF_CUDA_TRY(cudaEventCreateWithFlags(&hp.copied_extra[b][k], cudaEventDisableTiming));
     }
   }
@@ -83,10 +83,15 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
   const size_t snap_t = (size_t)p->nfreq * p->npol * p->nx * p->ny;   // bytes per sample t
   const size_t win_bytes = snap_t * p->n_int;
   const size_t beam_win = (size_t)p->nfreq * p->mx * p->my;           // floats per window
-  // chunks of whole windows, about 256 MiB each (at least one window)
-  int64_t cw = (int64_t)((256ull << 20) / win_bytes);
-  if (cw < 1) cw = 1;
-  if (cw > nwin) cw = nwin;
+  // Chunks of whole windows holding about four waves of work items for the resident CTAs
+  // (a one-window chunk of 1024 channels is 1.1 waves, so its second wave runs nearly
+  // empty), at most 4 GiB of voltages per buffer, split evenly over the call.
+  const int64_t want_items = 4LL * p->nsm * 6;
+  int64_t cw = (want_items + p->nfreq - 1) / p->nfreq;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)((4ull << 30) / win_bytes));
+  cw = std::max<int64_t>(1, std::min(cw, std::min(cap, nwin)));
+  const int64_t nchunk = (nwin + cw - 1) / cw;
+  cw = (nwin + nchunk - 1) / nchunk;
   if (hp.stage_bytes < cw * win_bytes) {
     // all earlier work on the old buffers must be done before they are freed
     cudaStreamSynchronize(hp.copy);
@@ -94,12 +99,12 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
     cudaStreamSynchronize(st);
   }
   if (hp.stage_bytes < cw * win_bytes) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < HostPipe::kStages; ++b) {
       cudaFree(hp.stage[b]);
       hp.stage[b] = nullptr;
     }
     hp.stage_bytes = 0;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < HostPipe::kStages; ++b) {
       if (cudaMalloc(&hp.stage[b], cw * win_bytes) != cudaSuccess) {
         cudaGetLastError();
         return set_error(FFTBF_ENOMEM, "cannot allocate voltage staging");
@@ -119,9 +124,10 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
     if (rc != FFTBF_OK) return rc;
   }
 
-  int chunk = 0;
-  for (int64_t w0 = 0; w0 < nwin; w0 += cw, ++chunk) {
-    const int b = chunk & 1;
+  // the buffer rotation continues from the previous call, so its last chunks' compute
+  // overlaps this call's first copies
+  int b = hp.next;
+  for (int64_t w0 = 0; w0 < nwin; w0 += cw, b = (b + 1) % HostPipe::kStages) {
     const int64_t nw = std::min<int64_t>(cw, nwin - w0);
     // the chunk's bytes go over kCopyStreams concurrent copies (one engine rarely fills
     // the host link), each waiting until the previous user of buffer b has finished
@@ -145,6 +151,7 @@ extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t
     if (rc != FFTBF_OK) return rc;
     FFTBF_CUDA_TRY(cudaEventRecord(hp.freed[b], st));
   }
+  hp.next = b;
   if (n_tied > 0) {
     rc = fftbf_tied_beams(p, hp.beams, nwin, n_tied, u, v, hp.tied, stream);
     if (rc != FFTBF_OK) return rc;

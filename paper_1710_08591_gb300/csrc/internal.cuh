@@ -115,17 +115,20 @@ void tied_free(TiedTables& tt);
 // Staging of fftbf_execute_host: two voltage chunks, device outputs, copy stream.
 struct HostPipe {
   static constexpr int kCopyStreams = 4;   // parallel host-to-device copies per chunk
+  static constexpr int kStages = 3;        // staging buffers: a buffer is refilled after the
+                                           // compute three chunks back, so copies rarely wait
   cudaStream_t copy = nullptr;
   cudaStream_t copy_extra[kCopyStreams - 1] = {nullptr, nullptr, nullptr};
-  cudaEvent_t copied_extra[2][kCopyStreams - 1] = {};
-  cudaEvent_t copied[2] = {nullptr, nullptr};
-  cudaEvent_t freed[2] = {nullptr, nullptr};
-  uint8_t* stage[2] = {nullptr, nullptr};
+  cudaEvent_t copied_extra[kStages][kCopyStreams - 1] = {};
+  cudaEvent_t copied[kStages] = {};
+  cudaEvent_t freed[kStages] = {};
+  uint8_t* stage[kStages] = {};
   size_t stage_bytes = 0;
   float* beams = nullptr;
   size_t beams_cap = 0;
   float* tied = nullptr;
   size_t tied_cap = 0;
+  int next = 0;                            // staging buffer of the next chunk (kept across calls)
 };
 void host_pipe_free(HostPipe& hp);
 
