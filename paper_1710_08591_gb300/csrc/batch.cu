@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "beam_fp32.cuh"
+#include "beam_fp32_warp.cuh"
 
 namespace fftbf {
 
@@ -31,7 +32,18 @@ struct Variant { int mx, log2n; };
 // Shapes compiled into the batch kernel: the lattices of the batched workload.
 constexpr Variant kVariants[] = {{4, 9}, {8, 7}, {16, 5}, {2, 10}, {1, 11}, {3, 8}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+// Warp-per-transform variants of the same shapes (E-W size, N-S length / 32), used when the
+// N-S axis is at least 2x zero-padded; ids kNumVariants + index.
+struct WarpVariant { int mx, r; };
+constexpr WarpVariant kWarpVariants[] = {{4, 16}, {8, 4}, {2, 32}, {3, 8}};
+constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 }  // namespace bt
+
+template <int MX, int R>
+__device__ __noinline__ void batch_warp_item(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                             bool load_tables) {
+  warp_item<MX, R>(a, item, smem, load_tables);
+}
 
 
 // One work item of one job: all its snapshots, S per step, bytes double-buffered.
@@ -166,6 +178,10 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchJob* __re
       case 3: batch_item<2, 10>(J.a, item, smem, load); break;
       case 4: batch_item<1, 11>(J.a, item, smem, load); break;
       case 5: batch_item<3, 8>(J.a, item, smem, load); break;
+      case bt::kNumVariants + 0: batch_warp_item<4, 16>(J.a, item, smem, load); break;
+      case bt::kNumVariants + 1: batch_warp_item<8, 4>(J.a, item, smem, load); break;
+      case bt::kNumVariants + 2: batch_warp_item<2, 32>(J.a, item, smem, load); break;
+      case bt::kNumVariants + 3: batch_warp_item<3, 8>(J.a, item, smem, load); break;
       default: break;
     }
   }
@@ -179,16 +195,27 @@ struct TuneKey {
     return nx == o.nx && ny == o.ny && mx == o.mx && my == o.my && npol == o.npol && n_int == o.n_int;
   }
 };
+struct Tuned { int variant, S; };
 static std::mutex g_tune_mu;
-static std::vector<std::pair<TuneKey, int>> g_tuned;
+static std::vector<std::pair<TuneKey, Tuned>> g_tuned;
 
 static int variant_of(int mx, int my) {
   for (int v = 0; v < bt::kNumVariants; ++v)
     if (bt::kVariants[v].mx == mx && (1 << bt::kVariants[v].log2n) == my) return v;
   return -1;
 }
+// warp variant of a shape (needs the N-S input to fill at most half of the transform)
+static int warp_variant_of(int mx, int my, int nyf) {
+  for (int v = 0; v < bt::kNumWarpVariants; ++v)
+    if (bt::kWarpVariants[v].mx == mx && 32 * bt::kWarpVariants[v].r == my && 2 * nyf <= my)
+      return bt::kNumVariants + v;
+  return -1;
+}
+static bool is_warp(int variant) { return variant >= bt::kNumVariants; }
 
-static size_t item_smem(const BeamArgs& a) {
+static size_t item_smem(const BeamArgs& a, int variant) {
+  if (is_warp(variant))
+    return warp_item_smem(a.S, a.mx, a.nx, a.ny, bt::kWarpVariants[variant - bt::kNumVariants].r);
   const int nant = a.nx * a.ny;
   const size_t rawsz = ((size_t)a.S * nant + 15) & ~(size_t)15;
   return 2 * rawsz + sizeof(float2) * ((size_t)nant + (size_t)a.mx * a.nx + a.my +
@@ -212,7 +239,7 @@ int batch_launch_jobs(const BatchJob* h_jobs, int njobs, BatchJob* d_jobs,
   return FFTBF_OK;
 }
 
-size_t batch_item_smem(const BeamArgs& a) { return item_smem(a); }
+size_t batch_item_smem(const BeamArgs& a, int variant) { return item_smem(a, variant); }
 
 }  // namespace fftbf
 
@@ -223,6 +250,7 @@ struct fftbf_batch {
   std::vector<fftbf_plan*> plans;
   std::vector<int> order;          // job order: costliest items first
   std::vector<int> S;              // tuned snapshots per step, per plan
+  std::vector<int> V;              // tuned variant (generic or warp path), per plan
   std::vector<BatchJob> jobs;
   BatchJob* d_jobs = nullptr;
   unsigned long long* d_counter = nullptr;
@@ -260,7 +288,7 @@ static int launch_jobs(fftbf_batch* bb, int64_t total, cudaStream_t st) {
 
 // Time one single-job batch launch of plan p with S snapshots per step on `nwin`
 // windows of zero bytes (the kernel has no data-dependent control flow).
-static float time_candidate(fftbf_batch* bb, const fftbf_plan* p, int S, int64_t nwin,
+static float time_candidate(fftbf_batch* bb, const fftbf_plan* p, int variant, int S, int64_t nwin,
                             const uint8_t* dv, float* db, cudaStream_t st) {
   BatchJob J{};
   fill_args(p, J.a);
@@ -268,11 +296,11 @@ static float time_candidate(fftbf_batch* bb, const fftbf_plan* p, int S, int64_t
   J.a.volts = dv;
   J.a.beams = db;
   J.a.nwin = nwin;
-  J.variant = variant_of(p->mx, p->my);
+  J.variant = variant;
   J.item0 = 0;
   J.nitems = nwin * p->nfreq;
   if (cudaMemcpyAsync(bb->d_jobs, &J, sizeof(J), cudaMemcpyHostToDevice, st) != cudaSuccess) return 1e30f;
-  const size_t need = item_smem(J.a);
+  const size_t need = item_smem(J.a, variant);
   if (need > bb->smem) return 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -344,32 +372,53 @@ fftbf_batch* fftbf_batch_create(fftbf_plan* const* plans, int n) {
   if (e == cudaSuccess) {
     for (auto* p : bb->plans) {
       const TuneKey key{p->nx, p->ny, p->mx, p->my, p->npol, p->n_int};
-      int bestS = 0;
-      {
+      // FFTBF_BATCH_PATH=generic|warp restricts the candidates (a test hook; bypasses the
+      // process-wide cache)
+      const char* force = std::getenv("FFTBF_BATCH_PATH");
+      const bool only_generic = force && std::strcmp(force, "generic") == 0;
+      const bool only_warp = force && std::strcmp(force, "warp") == 0;
+      Tuned best_t{-1, 0};
+      if (!force) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto& kv : g_tuned)
-          if (kv.first == key) bestS = kv.second;
+          if (kv.first == key) best_t = kv.second;
       }
-      if (bestS == 0) {
+      if (best_t.S == 0) {
+        // candidates: the generic path at S = 1, 2, 4, ... snapshots per step, and the
+        // warp-per-transform path (its S is fixed by the E-W size)
         const int nsnap = p->n_int * p->npol;
+        const int gv = variant_of(p->mx, p->my);
         float best = 1e30f;
-        bestS = 1;
-        for (int S = 1; S <= nsnap && S * p->mx * p->my <= kMaxElems; S *= 2) {
+        best_t = {gv, 1};
+        BeamArgs aw;
+        fill_args(p, aw);
+        const int wv = only_generic ? -1 : warp_variant_of(p->mx, p->my, aw.nyf);
+        for (int S = 1; S <= nsnap && S * p->mx * p->my <= kMaxElems && !(only_warp && wv >= 0); S *= 2) {
           BeamArgs a;
           fill_args(p, a);
           a.S = S;
-          if (item_smem(a) > bb->smem) break;
-          const float ms = time_candidate(bb, p, S, 2, dv, db, st);
-          if (ms < best) { best = ms; bestS = S; }
+          if (item_smem(a, gv) > bb->smem) break;
+          const float ms = time_candidate(bb, p, gv, S, 2, dv, db, st);
+          if (ms < best) { best = ms; best_t = {gv, S}; }
         }
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned.push_back({key, bestS});
+        if (wv >= 0) {
+          aw.S = wt::kWarps / wt::gcd8(p->mx);
+          if (item_smem(aw, wv) <= bb->smem) {
+            const float ms = time_candidate(bb, p, wv, aw.S, 2, dv, db, st);
+            if (ms < best || only_warp) { best = ms; best_t = {wv, aw.S}; }
+          }
+        }
+        if (!force) {
+          std::lock_guard<std::mutex> lock(g_tune_mu);
+          g_tuned.push_back({key, best_t});
+        }
       }
-      bb->S.push_back(bestS);
+      bb->S.push_back(best_t.S);
+      bb->V.push_back(best_t.variant);
       BeamArgs a;
       fill_args(p, a);
-      a.S = bestS;
-      max_smem = std::max(max_smem, item_smem(a));
+      a.S = best_t.S;
+      max_smem = std::max(max_smem, item_smem(a, best_t.variant));
     }
     e = cudaGetLastError();
   }
@@ -428,7 +477,7 @@ int fftbf_batch_execute(fftbf_batch* bb, const uint8_t* const* volts_dev, int64_
     J.a.volts = volts_dev[i];
     J.a.beams = beams_dev[i];
     J.a.nwin = T / bb->plans[i]->n_int;
-    J.variant = variant_of(bb->plans[i]->mx, bb->plans[i]->my);
+    J.variant = bb->V[i];
     J.nitems = J.a.nwin * bb->plans[i]->nfreq;
     J.item0 = total;
     total += J.nitems;
@@ -473,6 +522,11 @@ size_t fftbf_batch_smem(const fftbf_batch* bb) { return bb->smem; }
 int fftbf_batch_tuned_steps(const fftbf_batch* bb, int i) {
   if (!bb || i < 0 || i >= (int)bb->plans.size()) return set_error(FFTBF_EINVAL, "bad batch index");
   return bb->S[i];
+}
+
+int fftbf_batch_tuned_variant(const fftbf_batch* bb, int i) {
+  if (!bb || i < 0 || i >= (int)bb->plans.size()) return set_error(FFTBF_EINVAL, "bad batch index");
+  return bb->V[i];
 }
 
 void fftbf_batch_destroy(fftbf_batch* bb) {

@@ -5,6 +5,7 @@
 #include <cstdlib>
 
 #include "beam_fp32.cuh"
+#include "beam_fp32_warp.cuh"
 
 namespace fftbf {
 
@@ -87,6 +88,8 @@ int launch_beams_fp32(const BeamArgs& a, int nsm, cudaStream_t st) {
   if (a.nwin <= 0) return FFTBF_OK;
   if (fp32_n512_supported(a) && !getenv_flag("FFTBF_FP32_GENERIC"))
     return launch_beams_fp32_n512(a, nsm, st);
+  if (fp32_warp_supported(a) && !getenv_flag("FFTBF_FP32_GENERIC"))
+    return launch_beams_fp32_warp(a, nsm, st);
   if (fp32_fft_supported(a.mx, a.my) && fft_smem_bytes(a) <= 200 * 1024) {
     int log2n = 0;
     while ((1 << log2n) < a.my) ++log2n;

@@ -1,0 +1,220 @@
+// FP32 form, one warp per N-S transform, for N = 32 R beams (R = 4, 8, 16, 32, i.e. 128 to
+// 1024 beams) over at most N/2 feeds (the zero padding of Eq. b2n-1), any E-W size up to
+// 8. It generalises the 512-beam kernel: N = 32 x R Cooley-Tukey with n = n2 + R n1 and
+// k = k1 + 32 k2, inputs with n1 >= 16 being the padding.
+//   pass 1: X1[n2][k1] = sum_{n1 < 16} x[n2 + R n1] W32^(n1 k1). The 32 outputs k1 of one
+//     n2 split into H = 32 / D classes k1 = H m + h, D = min(R, 16): class h is a D-point
+//     DFT of the inputs pre-twiddled by W32^(n1 h) and folded modulo D. A lane owns one
+//     (n2, h) pair (R <= 16) or both classes of one n2 (R = 32). Then X1 *= W_N^(n2 k1)
+//     and the tile is stored transposed, [k1][n2] with row stride R + 1.
+//   pass 2: lane k1, an R-point DFT over n2 gives X[k1 + 32 k2]; its |.|^2 goes into
+//     per-lane accumulators (Eq. bf), so no complex beam leaves the SM.
+// A CTA has 8 warps and runs S snapshots per step (S MX a multiple of 8, so each warp
+// owns the same J = S MX / 8 transforms every step); at the end of a window the partial
+// sums of the S snapshot slots are added in a fixed order. Only warp-level
+// synchronisation inside the transforms; two CTA barriers per step.
+#pragma once
+
+#include "beam_fp32.cuh"
+
+namespace fftbf {
+
+// 32-point DFT as two 16-point DFTs and one radix-2 combination.
+template <> struct Dft<32> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 w[16] = {
+        {1.000000000e+00f, -0.000000000e+00f}, {9.807852804e-01f, -1.950903220e-01f},
+        {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f},
+        {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
+        {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f},
+        {0.000000000e+00f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f},
+        {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+        {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
+        {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
+    float2 e[16], o[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      e[k] = v[2 * k];
+      o[k] = v[2 * k + 1];
+    }
+    Dft<16>::run(e);
+    Dft<16>::run(o);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 t = k == 0 ? o[0] : (k == 8 ? mul_mi(o[8]) : cmul(o[k], w[k]));
+      v[k] = cadd(e[k], t);
+      v[k + 16] = csub(e[k], t);
+    }
+  }
+};
+
+namespace wt {
+constexpr int kWarps = 8;
+__host__ __device__ constexpr int gcd8(int m) {
+  return m % 8 == 0 ? 8 : (m % 4 == 0 ? 4 : (m % 2 == 0 ? 2 : 1));
+}
+}  // namespace wt
+
+template <int MX, int R> struct WarpCfg {
+  static constexpr int N = 32 * R;
+  static constexpr int S = wt::kWarps / wt::gcd8(MX);   // snapshots per step
+  static constexpr int J = MX / wt::gcd8(MX);           // transforms per warp per step
+  static constexpr int REG = 32 * (R + 1);              // float2 slots per transform region
+  static constexpr int D = R < 16 ? R : 16;             // pass-1 DFT length
+  static constexpr int H = 32 / D;                      // k1 classes per n2
+};
+
+// Shared-memory bytes of one item of the warp path.
+__host__ __device__ inline size_t warp_item_smem(int S, int mx, int nx, int ny, int R) {
+  const size_t nant = (size_t)nx * ny;
+  const size_t rawsz = ((size_t)S * nant + 15) & ~(size_t)15;
+  return 2 * rawsz + sizeof(float2) * (nant + (size_t)mx * nx + 32 * (size_t)R + 32 +
+                                       (size_t)S * mx * 32 * (R + 1));
+}
+
+// One work item (window, channel): all its snapshots, S per step, bytes double-buffered
+// through cp.async. 256 threads. a.S must be WarpCfg<MX, R>::S and a.nyf <= N/2.
+template <int MX, int R>
+__device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                          bool load_tables) {
+  using C = WarpCfg<MX, R>;
+  constexpr int N = C::N, S = C::S, J = C::J, REG = C::REG, D = C::D, H = C::H;
+  const int nant = a.nx * a.ny;
+  const int rawsz = (S * nant + 15) & ~15;
+  float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
+  float2* exsm = wsm + nant;
+  float2* twk = exsm + MX * a.nx;          // [k1 32][n2 R] W_N^(n2 k1)
+  float2* w32 = twk + 32 * R;              // [32] W32^m
+  float2* regs = w32 + 32;                 // [S * MX][REG]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nsnap = a.n_int * a.npol;
+  const int niter = (nsnap + S - 1) / S;
+  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  if (load_tables) {
+    for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
+    for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
+    for (int i = threadIdx.x; i < 32 * R; i += kThreads) twk[i] = a.tw[(i % R) * (i / R)];
+    for (int i = threadIdx.x; i < 32; i += kThreads) w32[i] = a.tw[i * R];
+  }
+  float acc[J][R];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[j][k] = 0.f;
+
+  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  cp_async_commit();
+  for (int it = 0; it < niter; ++it) {
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();                                  // bytes of `it` visible; regions free
+    // ---- unpack x weight, E-W transform -> region (s MX + A), slot (iy mod R) + (R+1)(iy / R)
+    const uint8_t* raw = smem + (it & 1) * rawsz;
+    for (int c = threadIdx.x; c < S * (N / 2); c += kThreads) {
+      const int s = c / (N / 2), iy = c - s * (N / 2);
+      float2 z[MX];
+#pragma unroll
+      for (int A = 0; A < MX; ++A) z[A] = czero();
+      if (iy < a.nyf && it * S + s < nsnap) {
+        const uint8_t* rs = raw + s * nant;
+        if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
+          if (a.ew_dft) {
+#pragma unroll
+            for (int ix = 0; ix < MX; ++ix) z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+            Dft<MX>::run(z);
+          }
+        }
+        if (!a.ew_dft) {
+          for (int ix = 0; ix < a.nx; ++ix) {
+            const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+#pragma unroll
+            for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
+          }
+        }
+      }
+      const int slot = (iy % R) + (R + 1) * (iy / R);
+#pragma unroll
+      for (int A = 0; A < MX; ++A) regs[(s * MX + A) * REG + slot] = z[A];
+    }
+    __syncthreads();                                  // regions written
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      float2* rg = regs + (warp + wt::kWarps * j) * REG;
+      // ---- pass 1
+      if constexpr (R <= 16) {
+        const int n2 = lane % R, h = lane / R;
+        float2 y[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) y[q] = czero();
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1)
+          y[n1 % D] = cadd(y[n1 % D], cmul(rg[n2 + (R + 1) * n1], w32[(n1 * h) & 31]));
+        Dft<D>::run(y);
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          const int k1 = H * m + h;
+          rg[k1 * (R + 1) + n2] = cmul(y[m], twk[k1 * R + n2]);
+        }
+      } else {
+        const int n2 = lane;
+        float2 x[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) x[n1] = rg[n2 + (R + 1) * n1];
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float2 y[16];
+#pragma unroll
+          for (int n1 = 0; n1 < 16; ++n1) y[n1] = h ? cmul(x[n1], w32[n1]) : x[n1];
+          Dft<16>::run(y);
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const int k1 = 2 * m + h;
+            rg[k1 * (R + 1) + n2] = cmul(y[m], twk[k1 * R + n2]);
+          }
+        }
+      }
+      __syncwarp();
+      // ---- pass 2: lane k1
+      {
+        float2 v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = rg[lane * (R + 1) + q];
+        Dft<R>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R; ++k2) acc[j][k2] = fmaf(v[k2].x, v[k2].x, fmaf(v[k2].y, v[k2].y, acc[j][k2]));
+      }
+    }
+  }
+  // ---- window complete: add the S snapshot slots of each E-W beam in order, write once
+  float* dst = a.beams + item * (int64_t)(MX * N);
+  if constexpr (S == 1 && J == 1) {
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) dst[warp * N + lane + 32 * k2] = acc[0][k2];
+    __syncthreads();
+  } else {
+    __syncthreads();
+    float* red = reinterpret_cast<float*>(regs);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) red[(warp + wt::kWarps * j) * N + lane + 32 * k2] = acc[j][k2];
+    __syncthreads();
+    for (int o = threadIdx.x; o < MX * N; o += kThreads) {
+      const int A = o / N, k = o - A * N;
+      float sum = 0.f;
+#pragma unroll
+      for (int s = 0; s < S; ++s) sum += red[(s * MX + A) * N + k];
+      dst[o] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// Standalone launch for fftbf_execute (beam_fp32_warp.cu).
+bool fp32_warp_supported(const BeamArgs& a);
+int launch_beams_fp32_warp(const BeamArgs& a, int nsm, cudaStream_t st);
+
+}  // namespace fftbf

@@ -61,7 +61,7 @@ struct BatchJob {
   int64_t nitems;     // nwin * nfreq
 };
 int batch_variant(int mx, int my);
-size_t batch_item_smem(const BeamArgs& a);
+size_t batch_item_smem(const BeamArgs& a, int variant);
 // Upload h_jobs (item0 must be prefix sums) and run the batch kernel over them.
 int batch_launch_jobs(const BatchJob* h_jobs, int njobs, BatchJob* d_jobs,
                       unsigned long long* d_counter, size_t smem, int grid, cudaStream_t st);
@@ -140,6 +140,7 @@ namespace fftbf {
 void batch_fill_args(const fftbf_plan* p, BeamArgs& a);
 }
 extern "C" int fftbf_batch_grid(const fftbf_batch* bb);
+extern "C" int fftbf_batch_tuned_variant(const fftbf_batch* bb, int i);
 extern "C" size_t fftbf_batch_smem(const fftbf_batch* bb);
 
 struct fftbf_plan {

@@ -65,6 +65,7 @@ struct fftbf_server {
   std::vector<fftbf_plan*> lattices;
   fftbf_batch* tuner = nullptr;          // owns the tuned tile per lattice
   std::vector<int> S;
+  std::vector<int> V;                    // tuned variant per lattice (generic or warp path)
   size_t smem = 0;
   int grid = 0;
   size_t slot_bytes = 0, frame_off = 0;
@@ -131,7 +132,7 @@ void run_scheduler(fftbf_server* sv) {
         J.a.volts = slot;
         J.a.beams = reinterpret_cast<float*>(slot + sv->frame_off);
         J.a.nwin = 1;
-        J.variant = batch_variant(p->mx, p->my);
+        J.variant = sv->V[f.lattice];
         J.nitems = p->nfreq;
         J.item0 = total;
         total += J.nitems;
@@ -201,7 +202,10 @@ fftbf_server* fftbf_server_create(fftbf_plan* const* lattices, int n, int64_t hb
   cudaSetDevice(sv->device);
   sv->tuner = fftbf_batch_create(lattices, n);
   if (!sv->tuner) { delete sv; cudaSetDevice(prev); return nullptr; }
-  for (int i = 0; i < n; ++i) sv->S.push_back(fftbf_batch_tuned_steps(sv->tuner, i));
+  for (int i = 0; i < n; ++i) {
+    sv->S.push_back(fftbf_batch_tuned_steps(sv->tuner, i));
+    sv->V.push_back(fftbf_batch_tuned_variant(sv->tuner, i));
+  }
   sv->smem = fftbf_batch_smem(sv->tuner);
   sv->grid = fftbf_batch_grid(sv->tuner);
   size_t max_in = 0, max_out = 0;

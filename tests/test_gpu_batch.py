@@ -61,6 +61,21 @@ def test_batch_matches_oracle_every_array():
         assert err.max() <= TOL_BEAM, (a["shape"], err.max())
 
 
+@pytest.mark.parametrize("path", ["generic", "warp"])
+def test_batch_each_path_matches_oracle(path, monkeypatch):
+    """Both transform paths of the batch kernel, forced in turn (the warp-per-transform
+    path covers the 2x-padded 4x512, 8x128, 2x1024 and 3x256 shapes; the others stay
+    generic)."""
+    monkeypatch.setenv("FFTBF_BATCH_PATH", path)
+    T, n_int = 24, 12
+    arrs = _arrays([2, 3, 2, 2, 1, 3], T, n_int, seed=70)
+    got, _ = _run(arrs, T)
+    for a, g in zip(arrs, got):
+        nx, ny, mx, my, npol, nf, n_int_ = a["shape"]
+        ref = oracle_beams(a["v"], a["w"], nx, ny, mx, my, npol, nf, n_int_)
+        assert (np.abs(g - ref) / ref).max() <= TOL_BEAM, (path, a["shape"])
+
+
 def test_batch_bit_identical_alone_and_in_mix_and_replayed():
     T, n_int = 64, 32
     arrs = _arrays([2, 3, 2, 2, 1, 2], T, n_int, seed=50)

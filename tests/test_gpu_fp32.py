@@ -65,6 +65,11 @@ CASES = [
     (2, 200, 2, 512, 1, 2, 14, 7, "half_sine"),     # 512-beam kernel, 200 feeds, ragged
     (8, 256, 8, 512, 2, 2, 16, 8, "random"),        # 512-beam kernel, 8 warps
     (3, 256, 4, 512, 2, 2, 16, 8, "random"),        # 512-beam kernel, E-W padded 3 -> 4
+    (1, 50, 1, 128, 2, 3, 48, 16, "random"),        # warp path: 128 beams, 8 snapshots/step
+    (2, 100, 2, 256, 1, 2, 30, 10, "half_sine"),    # warp path: ragged (10 snapshots, 4/step)
+    (5, 128, 3, 256, 2, 2, 24, 12, "random"),       # warp path: E-W 5 folded onto 3
+    (1, 300, 1, 1024, 2, 2, 16, 8, "random"),       # warp path: 1024 beams, E-W 1
+    (4, 33, 4, 128, 2, 2, 16, 8, "random"),         # warp path: 33 feeds, 2 snapshots/step
 ]
 
 
@@ -80,9 +85,11 @@ def test_beams_match_oracle(case):
     assert err.max() <= TOL_BEAM, f"max rel err {err.max():.3g}"
 
 
-@pytest.mark.parametrize("case", [c for c in CASES if c[3] == 512], ids=lambda c: "x".join(map(str, c[:4])))
-def test_generic_kernel_on_512_shapes(case, monkeypatch):
-    """The generic Stockham kernel, forced on shapes the 512-beam kernel normally takes."""
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] in (128, 256, 512, 1024) and 2 * c[1] <= c[3]],
+                         ids=lambda c: "x".join(map(str, c[:4])))
+def test_generic_kernel_on_warp_shapes(case, monkeypatch):
+    """The generic Stockham kernel, forced on shapes the warp-per-transform kernels (and
+    the 512-beam kernel) normally take."""
     monkeypatch.setenv("FFTBF_FP32_GENERIC", "1")
     nx, ny, mx, my, npol, nfreq, T, n_int, wk = case
     v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights=wk, seed=4)
