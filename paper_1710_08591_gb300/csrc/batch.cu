@@ -32,10 +32,11 @@ struct Variant { int mx, log2n; };
 // Shapes compiled into the batch kernel: the lattices of the batched workload.
 constexpr Variant kVariants[] = {{4, 9}, {8, 7}, {16, 5}, {2, 10}, {1, 11}, {3, 8}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
-// Warp-per-transform variants of the same shapes (E-W size, N-S length / 32), used when the
-// N-S axis is at least 2x zero-padded; ids kNumVariants + index.
-struct WarpVariant { int mx, r; };
-constexpr WarpVariant kWarpVariants[] = {{4, 16}, {8, 4}, {2, 32}, {3, 8}};
+// Warp-per-transform variants of the same shapes (E-W size, N-S length), used when the
+// N-S axis is at least 2x zero-padded; ids kNumVariants + index. 2048 beams take a warp
+// pair per transform, 32 beams x 16 E-W beams a lane per transform.
+struct WarpVariant { int mx, my; };
+constexpr WarpVariant kWarpVariants[] = {{4, 512}, {8, 128}, {2, 1024}, {3, 256}, {1, 2048}, {16, 32}};
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 }  // namespace bt
 
@@ -43,6 +44,14 @@ template <int MX, int R>
 __device__ __noinline__ void batch_warp_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                              bool load_tables) {
   warp_item<MX, R>(a, item, smem, load_tables);
+}
+__device__ __noinline__ void batch_warp2_item(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                              bool load_tables) {
+  warp2_item<1>(a, item, smem, load_tables);
+}
+__device__ __noinline__ void batch_lane16_item(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                               bool load_tables) {
+  lane_item16(a, item, smem, load_tables);
 }
 
 
@@ -182,6 +191,8 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchJob* __re
       case bt::kNumVariants + 1: batch_warp_item<8, 4>(J.a, item, smem, load); break;
       case bt::kNumVariants + 2: batch_warp_item<2, 32>(J.a, item, smem, load); break;
       case bt::kNumVariants + 3: batch_warp_item<3, 8>(J.a, item, smem, load); break;
+      case bt::kNumVariants + 4: batch_warp2_item(J.a, item, smem, load); break;
+      case bt::kNumVariants + 5: batch_lane16_item(J.a, item, smem, load); break;
       default: break;
     }
   }
@@ -207,15 +218,26 @@ static int variant_of(int mx, int my) {
 // warp variant of a shape (needs the N-S input to fill at most half of the transform)
 static int warp_variant_of(int mx, int my, int nyf) {
   for (int v = 0; v < bt::kNumWarpVariants; ++v)
-    if (bt::kWarpVariants[v].mx == mx && 32 * bt::kWarpVariants[v].r == my && 2 * nyf <= my)
+    if (bt::kWarpVariants[v].mx == mx && bt::kWarpVariants[v].my == my && 2 * nyf <= my)
       return bt::kNumVariants + v;
   return -1;
 }
 static bool is_warp(int variant) { return variant >= bt::kNumVariants; }
+// snapshots per step of a warp variant (fixed by its layout)
+static int warp_variant_S(int variant) {
+  const bt::WarpVariant& w = bt::kWarpVariants[variant - bt::kNumVariants];
+  if (w.my == 2048) return 4 / w.mx;
+  if (w.my == 32) return kLaneS;
+  return wt::kWarps / wt::gcd8(w.mx);
+}
 
 static size_t item_smem(const BeamArgs& a, int variant) {
-  if (is_warp(variant))
-    return warp_item_smem(a.S, a.mx, a.nx, a.ny, bt::kWarpVariants[variant - bt::kNumVariants].r);
+  if (is_warp(variant)) {
+    const bt::WarpVariant& w = bt::kWarpVariants[variant - bt::kNumVariants];
+    if (w.my == 2048) return warp2_item_smem(a.S, a.mx, a.nx, a.ny);
+    if (w.my == 32) return lane_item_smem(a.nx, a.ny);
+    return warp_item_smem(a.S, a.mx, a.nx, a.ny, w.my / 32);
+  }
   const int nant = a.nx * a.ny;
   const size_t rawsz = ((size_t)a.S * nant + 15) & ~(size_t)15;
   return 2 * rawsz + sizeof(float2) * ((size_t)nant + (size_t)a.mx * a.nx + a.my +
@@ -402,7 +424,7 @@ fftbf_batch* fftbf_batch_create(fftbf_plan* const* plans, int n) {
           if (ms < best) { best = ms; best_t = {gv, S}; }
         }
         if (wv >= 0) {
-          aw.S = wt::kWarps / wt::gcd8(p->mx);
+          aw.S = warp_variant_S(wv);
           if (item_smem(aw, wv) <= bb->smem) {
             const float ms = time_candidate(bb, p, wv, aw.S, 2, dv, db, st);
             if (ms < best || only_warp) { best = ms; best_t = {wv, aw.S}; }

@@ -19,18 +19,23 @@
 
 namespace fftbf {
 
+// W32^k = exp(-2 pi i k / 32), k < 16.
+__device__ __forceinline__ float2 w32c(int k) {
+  const float2 w[16] = {
+      {1.000000000e+00f, -0.000000000e+00f}, {9.807852804e-01f, -1.950903220e-01f},
+      {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f},
+      {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
+      {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f},
+      {0.000000000e+00f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f},
+      {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
+      {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
+      {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
+  return w[k];
+}
+
 // 32-point DFT as two 16-point DFTs and one radix-2 combination.
 template <> struct Dft<32> {
   __device__ __forceinline__ static void run(float2* v) {
-    const float2 w[16] = {
-        {1.000000000e+00f, -0.000000000e+00f}, {9.807852804e-01f, -1.950903220e-01f},
-        {9.238795325e-01f, -3.826834324e-01f}, {8.314696123e-01f, -5.555702330e-01f},
-        {7.071067812e-01f, -7.071067812e-01f}, {5.555702330e-01f, -8.314696123e-01f},
-        {3.826834324e-01f, -9.238795325e-01f}, {1.950903220e-01f, -9.807852804e-01f},
-        {0.000000000e+00f, -1.000000000e+00f}, {-1.950903220e-01f, -9.807852804e-01f},
-        {-3.826834324e-01f, -9.238795325e-01f}, {-5.555702330e-01f, -8.314696123e-01f},
-        {-7.071067812e-01f, -7.071067812e-01f}, {-8.314696123e-01f, -5.555702330e-01f},
-        {-9.238795325e-01f, -3.826834324e-01f}, {-9.807852804e-01f, -1.950903220e-01f}};
     float2 e[16], o[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -41,7 +46,7 @@ template <> struct Dft<32> {
     Dft<16>::run(o);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const float2 t = k == 0 ? o[0] : (k == 8 ? mul_mi(o[8]) : cmul(o[k], w[k]));
+      const float2 t = k == 0 ? o[0] : (k == 8 ? mul_mi(o[8]) : cmul(o[k], w32c(k)));
       v[k] = cadd(e[k], t);
       v[k + 16] = csub(e[k], t);
     }
@@ -63,6 +68,42 @@ template <int MX, int R> struct WarpCfg {
   static constexpr int D = R < 16 ? R : 16;             // pass-1 DFT length
   static constexpr int H = 32 / D;                      // k1 classes per n2
 };
+
+// Unpack x weight and E-W transform of S snapshots into per-transform regions:
+// region (s MX + A), slot (iy mod R) + stride (iy / R), for the feeds iy < NH (zeros
+// past nyf and past the last snapshot).
+template <int MX, int R, int NH>
+__device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* raw, int S, int it,
+                                              int nsnap, int nant, const float2* wsm,
+                                              const float2* exsm, float2* regs, int reg,
+                                              int stride) {
+  for (int c = threadIdx.x; c < S * NH; c += kThreads) {
+    const int s = c / NH, iy = c - s * NH;
+    float2 z[MX];
+#pragma unroll
+    for (int A = 0; A < MX; ++A) z[A] = czero();
+    if (iy < a.nyf && it * S + s < nsnap) {
+      const uint8_t* rs = raw + s * nant;
+      if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8 || MX == 16) {
+        if (a.ew_dft) {
+#pragma unroll
+          for (int ix = 0; ix < MX; ++ix) z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+          Dft<MX>::run(z);
+        }
+      }
+      if (!a.ew_dft) {
+        for (int ix = 0; ix < a.nx; ++ix) {
+          const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+#pragma unroll
+          for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
+        }
+      }
+    }
+    const int slot = (iy % R) + stride * (iy / R);
+#pragma unroll
+    for (int A = 0; A < MX; ++A) regs[(s * MX + A) * reg + slot] = z[A];
+  }
+}
 
 // Shared-memory bytes of one item of the warp path.
 __host__ __device__ inline size_t warp_item_smem(int S, int mx, int nx, int ny, int R) {
@@ -110,33 +151,8 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
     cp_async_wait<1>();
     __syncthreads();                                  // bytes of `it` visible; regions free
     // ---- unpack x weight, E-W transform -> region (s MX + A), slot (iy mod R) + (R+1)(iy / R)
-    const uint8_t* raw = smem + (it & 1) * rawsz;
-    for (int c = threadIdx.x; c < S * (N / 2); c += kThreads) {
-      const int s = c / (N / 2), iy = c - s * (N / 2);
-      float2 z[MX];
-#pragma unroll
-      for (int A = 0; A < MX; ++A) z[A] = czero();
-      if (iy < a.nyf && it * S + s < nsnap) {
-        const uint8_t* rs = raw + s * nant;
-        if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
-          if (a.ew_dft) {
-#pragma unroll
-            for (int ix = 0; ix < MX; ++ix) z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
-            Dft<MX>::run(z);
-          }
-        }
-        if (!a.ew_dft) {
-          for (int ix = 0; ix < a.nx; ++ix) {
-            const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
-#pragma unroll
-            for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
-          }
-        }
-      }
-      const int slot = (iy % R) + (R + 1) * (iy / R);
-#pragma unroll
-      for (int A = 0; A < MX; ++A) regs[(s * MX + A) * REG + slot] = z[A];
-    }
+    warp_ew_stage<MX, R, N / 2>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
+                                REG, R + 1);
     __syncthreads();                                  // regions written
 #pragma unroll
     for (int j = 0; j < J; ++j) {
@@ -213,7 +229,183 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
   }
 }
 
-// Standalone launch for fftbf_execute (beam_fp32_warp.cu).
+// ---- 2048 beams (N = 32 x 64): two warps per transform --------------------------------
+// Warp g of a pair runs pass 1 for n2 = 32 g + lane (both classes h of a 16-point DFT over
+// the 16 nonzero n1), the pair meets on a named barrier, and in pass 2 warp g takes the
+// outputs k2 = 2 m + g: X[k1 + 32 k2] = sum_{n2 < 32} u_g[n2] W32^(n2 m) with
+// u_0 = T[n2] + T[n2 + 32] and u_1 = (T[n2] - T[n2 + 32]) W64^n2 (a radix-2 split of the
+// 64-point DFT over n2), so each lane keeps 32 accumulators.
+template <int MX> struct Warp2Cfg {
+  static constexpr int N = 2048, R = 64, S = 4 / MX, REG = 32 * (R + 1);
+};
+__host__ __device__ inline size_t warp2_item_smem(int S, int mx, int nx, int ny) {
+  const size_t nant = (size_t)nx * ny;
+  const size_t rawsz = ((size_t)S * nant + 15) & ~(size_t)15;
+  return 2 * rawsz + sizeof(float2) * (nant + (size_t)mx * nx + 32 * 64 + 32 + 32 +
+                                       (size_t)S * mx * 32 * 65);
+}
+
+template <int MX>
+__device__ __forceinline__ void warp2_item(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                           bool load_tables) {
+  using C = Warp2Cfg<MX>;
+  constexpr int N = C::N, R = C::R, S = C::S, REG = C::REG;
+  const int nant = a.nx * a.ny;
+  const int rawsz = (S * nant + 15) & ~15;
+  float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
+  float2* exsm = wsm + nant;
+  float2* twk = exsm + MX * a.nx;          // [k1 32][n2 64] W_N^(n2 k1)
+  float2* w32 = twk + 32 * R;              // [32] W32^m
+  float2* w64 = w32 + 32;                  // [32] W64^n
+  float2* regs = w64 + 32;                 // [S * MX][REG]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pair = warp >> 1, g = warp & 1;
+  const int nsnap = a.n_int * a.npol;
+  const int niter = (nsnap + S - 1) / S;
+  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  if (load_tables) {
+    for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
+    for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
+    for (int i = threadIdx.x; i < 32 * R; i += kThreads) twk[i] = a.tw[(i % R) * (i / R)];
+    for (int i = threadIdx.x; i < 32; i += kThreads) {
+      w32[i] = a.tw[i * 64];
+      w64[i] = a.tw[i * 32];
+    }
+  }
+  float acc[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  cp_async_commit();
+  for (int it = 0; it < niter; ++it) {
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    warp_ew_stage<MX, R, N / 2>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
+                                REG, R + 1);
+    __syncthreads();
+    float2* rg = regs + pair * REG;          // transform `pair` of this step
+    {
+      const int n2 = 32 * g + lane;
+      float2 x[16];
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) x[n1] = rg[n2 + (R + 1) * n1];
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float2 y[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) y[n1] = h ? cmul(x[n1], w32[n1]) : x[n1];
+        Dft<16>::run(y);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int k1 = 2 * m + h;
+          rg[k1 * (R + 1) + n2] = cmul(y[m], twk[k1 * R + n2]);
+        }
+      }
+    }
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + pair), "r"(64) : "memory");
+    {
+      float2 u[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float2 lo = rg[lane * (R + 1) + q], hi = rg[lane * (R + 1) + q + 32];
+        u[q] = g == 0 ? cadd(lo, hi) : cmul(csub(lo, hi), w64[q]);
+      }
+      Dft<32>::run(u);
+#pragma unroll
+      for (int m = 0; m < 32; ++m) acc[m] = fmaf(u[m].x, u[m].x, fmaf(u[m].y, u[m].y, acc[m]));
+    }
+  }
+  // ---- window complete: slot (pair) holds (s, A) = (pair / MX, pair % MX)
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(regs);
+#pragma unroll
+  for (int m = 0; m < 32; ++m) red[pair * N + lane + 32 * (2 * m + g)] = acc[m];
+  __syncthreads();
+  float* dst = a.beams + item * (int64_t)(MX * N);
+  for (int o = threadIdx.x; o < MX * N; o += kThreads) {
+    const int A = o / N, k = o - A * N;
+    float sum = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) sum += red[(s * MX + A) * N + k];
+    dst[o] = sum;
+  }
+  __syncthreads();
+}
+
+// ---- 32 beams over at most 16 feeds, 16 E-W beams: one lane per transform ------------
+// 256 transforms per step (S = 16 snapshots x 16 E-W beams); lane t reads its 16 inputs
+// (row stride 17) and forms the 32 outputs as two 16-point DFTs (inputs x and x W32^n),
+// squaring them into 32 accumulators.
+constexpr int kLaneS = 16;
+__host__ __device__ inline size_t lane_item_smem(int nx, int ny) {
+  const size_t nant = (size_t)nx * ny;
+  const size_t rawsz = ((size_t)kLaneS * nant + 15) & ~(size_t)15;
+  return 2 * rawsz + sizeof(float2) * (nant + (size_t)16 * nx + (size_t)kLaneS * 16 * 17);
+}
+
+__device__ __forceinline__ void lane_item16(const BeamArgs& a, int64_t item, unsigned char* smem,
+                                            bool load_tables) {
+  constexpr int MX = 16, N = 32, S = kLaneS, REG = 17;
+  const int nant = a.nx * a.ny;
+  const int rawsz = (S * nant + 15) & ~15;
+  float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
+  float2* exsm = wsm + nant;
+  float2* regs = exsm + MX * a.nx;         // [S * MX][17]
+  const int t = threadIdx.x;               // transform (s, A) = (t / 16, t % 16)
+  const int nsnap = a.n_int * a.npol;
+  const int niter = (nsnap + S - 1) / S;
+  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  if (load_tables) {
+    for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
+    for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
+  }
+  float acc[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) acc[k] = 0.f;
+  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  cp_async_commit();
+  for (int it = 0; it < niter; ++it) {
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    warp_ew_stage<MX, 16, 16>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs, REG, 17);
+    __syncthreads();
+    float2 x[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) x[n] = regs[t * REG + n];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float2 y[16];
+#pragma unroll
+      for (int n = 0; n < 16; ++n) y[n] = h ? cmul(x[n], w32c(n)) : x[n];
+      Dft<16>::run(y);
+#pragma unroll
+      for (int m = 0; m < 16; ++m)
+        acc[2 * m + h] = fmaf(y[m].x, y[m].x, fmaf(y[m].y, y[m].y, acc[2 * m + h]));
+    }
+  }
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(regs);
+#pragma unroll
+  for (int k = 0; k < N; ++k) red[t * N + k] = acc[k];
+  __syncthreads();
+  float* dst = a.beams + item * (int64_t)(MX * N);
+  for (int o = threadIdx.x; o < MX * N; o += kThreads) {
+    const int A = o / N, k = o - A * N;
+    float sum = 0.f;
+#pragma unroll
+    for (int s = 0; s < S; ++s) sum += red[(s * MX + A) * N + k];
+    dst[o] = sum;
+  }
+  __syncthreads();
+}
+
+// Standalone launch for fftbf_execute (beam_fp32_warp.cu): 128..1024 beams (one warp per
+// transform), 2048 beams (a warp pair per transform), 32 beams x 16 E-W (a lane each).
 bool fp32_warp_supported(const BeamArgs& a);
 int launch_beams_fp32_warp(const BeamArgs& a, int nsm, cudaStream_t st);
 

@@ -70,6 +70,8 @@ CASES = [
     (5, 128, 3, 256, 2, 2, 24, 12, "random"),       # warp path: E-W 5 folded onto 3
     (1, 300, 1, 1024, 2, 2, 16, 8, "random"),       # warp path: 1024 beams, E-W 1
     (4, 33, 4, 128, 2, 2, 16, 8, "random"),         # warp path: 33 feeds, 2 snapshots/step
+    (2, 700, 2, 2048, 1, 2, 12, 6, "random"),       # 2048 beams, a warp pair per transform
+    (12, 10, 16, 32, 2, 2, 40, 20, "random"),       # 32 beams, a lane per transform; E-W 12 -> 16
 ]
 
 
@@ -85,7 +87,7 @@ def test_beams_match_oracle(case):
     assert err.max() <= TOL_BEAM, f"max rel err {err.max():.3g}"
 
 
-@pytest.mark.parametrize("case", [c for c in CASES if c[3] in (128, 256, 512, 1024) and 2 * c[1] <= c[3]],
+@pytest.mark.parametrize("case", [c for c in CASES if c[3] in (32, 128, 256, 512, 1024, 2048) and 2 * c[1] <= c[3]],
                          ids=lambda c: "x".join(map(str, c[:4])))
 def test_generic_kernel_on_warp_shapes(case, monkeypatch):
     """The generic Stockham kernel, forced on shapes the warp-per-transform kernels (and
