@@ -81,6 +81,136 @@ __global__ void tied_table_kernel(int n, int M, int mode, const double* g, int t
   }
 }
 
+// Dirichlet tables (mode 0), one CTA per (f, pointing) row at a time, by angle addition:
+// with e = y - k/M and L = 2n - 1,
+//   sin(L pi e) = sin(L pi y) cos(L pi k/M) - cos(L pi y) sin(L pi k/M),
+//   sin(pi e)   = sin(pi y) cos(pi k/M) - cos(pi y) sin(pi k/M),
+// from FP64 sines of the row (two sincospi per row) and of the beams (a shared-memory table,
+// L k reduced modulo 2M in integers), so a weight costs a few FP64 multiply-adds instead of
+// two sincospi and a division (FP64 is slow on this part); the ratio of the two FP64 sines
+// is taken in FP32, the precision of the table. Limit L/M for |e| < 1e-9.
+__global__ void __launch_bounds__(256) tied_dirichlet_table_kernel(int n, int M, int trunc, int nfreq,
+                                                                   int n_tied, const double* y,
+                                                                   const int* perm, float* out) {
+  extern __shared__ double2 dtab[];      // [M][2]: (cos, sin)(pi k/M), (cos, sin)(L pi k/M)
+  __shared__ double row[5];              // sin, cos of pi y and L pi y; y
+  const int L = 2 * n - 1;
+  const double invM = 1.0 / (double)M;
+  const float invMf = (float)invM;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    double s1, c1, sL, cL;
+    sincospi((double)k / (double)M, &s1, &c1);
+    sincospi((double)(((long long)L * k) % (2LL * M)) / (double)M, &sL, &cL);
+    dtab[2 * k] = make_double2(c1, s1);
+    dtab[2 * k + 1] = make_double2(cL, sL);
+  }
+  const int64_t rows = (int64_t)nfreq * n_tied;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    __syncthreads();                     // tables ready; previous row's values consumed
+    if (threadIdx.x == 0) {
+      const int f = (int)(r / n_tied);
+      const double yv = y[(int64_t)f * n_tied + perm[r]];
+      sincospi(yv, &row[0], &row[1]);
+      sincospi((double)L * yv, &row[2], &row[3]);
+      row[4] = yv;
+    }
+    __syncthreads();
+    const double sy = row[0], cy = row[1], sLy = row[2], cLy = row[3], yv = row[4];
+    const int first = trunc > 0 ? first_tap(M, 0, yv, trunc) : 0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+      double e = fma(-(double)k, invM, yv);
+      e -= rint(e);
+      float w;
+      if (fabs(e) < 1e-9) {
+        w = (float)L * invMf;
+      } else {
+        const double2 t1 = dtab[2 * k], tL = dtab[2 * k + 1];
+        const double num = sLy * tL.x - cLy * tL.y;
+        const double den = sy * t1.x - cy * t1.y;
+        w = (float)num / (float)den * invMf;     // FP64 sines, their ratio in FP32
+      }
+      if (trunc > 0 && (k - first + M) % M >= trunc) w = 0.f;
+      out[r * M + k] = w;
+    }
+  }
+}
+
+// Windowed tables (mode 2) for a power-of-two M, one CTA per row at a time: the kernel is a
+// trigonometric polynomial of degree n - 1, sampled at the M beams,
+//   w(y - j/M) = (1/M) Re sum_{d < n} a_d exp(-2 pi i d y) exp(+2 pi i d j / M),
+// a_0 = g_0, a_d = 2 g_d (real symmetric lags), i.e. one inverse DFT of length M per
+// pointing: radix-2 Stockham in FP64 in shared memory, O(M log M) per row instead of the
+// O(M n) direct sums.
+__global__ void __launch_bounds__(256) tied_window_table_kernel(int n, int M, const double* g,
+                                                                int trunc, int nfreq, int n_tied,
+                                                                const double* y, const int* perm,
+                                                                float* out) {
+  extern __shared__ double2 wsm2[];
+  const int half = M >> 1;
+  double2* twp = wsm2;                   // [M/2] exp(+2 pi i m / M)
+  double2* b0 = twp + half;              // [M]
+  double2* b1 = b0 + M;                  // [M]
+  __shared__ double rowy;
+  __shared__ double2 zlo[16], zhi[128];  // exp(-2 pi i d y) = zlo[d mod 16] zhi[d / 16], n <= 2048
+  for (int m = threadIdx.x; m < half; m += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)M, &s, &c);
+    twp[m] = make_double2(c, s);
+  }
+  const int64_t rows = (int64_t)nfreq * n_tied;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) rowy = y[(int64_t)(r / n_tied) * n_tied + perm[r]];
+    __syncthreads();
+    const double yv = rowy;
+    // the phases of the row: 16 + n/16 sincospi instead of n
+    {
+      const int t = threadIdx.x;
+      const int m = t < 16 ? t : 16 * (t - 16);
+      if (t < 16 + (n + 15) / 16) {
+        double ph = (double)m * yv;
+        ph -= rint(ph);
+        double sn, cs;
+        sincospi(-2.0 * ph, &sn, &cs);
+        if (t < 16) zlo[t] = make_double2(cs, sn);
+        else zhi[t - 16] = make_double2(cs, sn);
+      }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < M; d += blockDim.x) {
+      double2 v = make_double2(0.0, 0.0);
+      if (d < n) {
+        const double2 p = zlo[d & 15], q = zhi[d >> 4];
+        const double a = d == 0 ? g[n - 1] : 2.0 * g[n - 1 + d];
+        v = make_double2(a * (p.x * q.x - p.y * q.y), a * (p.x * q.y + p.y * q.x));
+      }
+      b0[d] = v;
+    }
+    __syncthreads();
+    double2* src = b0;
+    double2* dst = b1;
+    for (int ns = 1; ns < M; ns <<= 1) {
+      for (int j = threadIdx.x; j < half; j += blockDim.x) {
+        const int k = j & (ns - 1);
+        const double2 w = twp[k * (half / ns)];
+        const double2 a = src[j], c = src[j + half];
+        const double2 b = make_double2(c.x * w.x - c.y * w.y, c.x * w.y + c.y * w.x);
+        const int d = ((j - k) << 1) + k;
+        dst[d] = make_double2(a.x + b.x, a.y + b.y);
+        dst[d + ns] = make_double2(a.x - b.x, a.y - b.y);
+      }
+      __syncthreads();
+      double2* t = src; src = dst; dst = t;
+    }
+    const int first = trunc > 0 ? first_tap(M, 2, yv, trunc) : 0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      double w = src[j].x / (double)M;
+      if (trunc > 0 && (j - first + M) % M >= trunc) w = 0.0;
+      out[r * M + j] = (float)w;
+    }
+  }
+}
+
 // Compact tables: per (f, pointing) the first kept beam of each axis and the kx + ky tap
 // weights (caller's pointing order).
 __global__ void tied_compact_table_kernel(int nx, int ny, int mx, int my, int mode_x,
@@ -212,6 +342,14 @@ void tied_free(TiedTables& tt) {
   tt = TiedTables();
 }
 
+// multiprocessors of the current device (grid sizing of the row kernels)
+static int tt_sms(cudaStream_t) {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
 int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int n_tied,
                  const double* u, const double* v, cudaStream_t st) {
   const size_t nuv = (size_t)nfreq * n_tied;
@@ -238,19 +376,24 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
                        "pointing %zu: v*pad_y = %.12g is off the FFT-beam grid and pad_y < "
                        "2ny-1, so no regridding kernel exists on that axis", i, v[i] * my);
   }
-  // Sort each frequency's pointings by E-W beam (one-hot axis) so tiles skip columns.
+  // Sort each frequency's pointings by E-W beam (one-hot axis) so tiles skip columns: a
+  // stable counting sort on the pad_x possible beams.
   std::vector<int> perm(nuv);
+  std::vector<int> key(dense_x ? 0 : n_tied), count(dense_x ? 0 : mx + 1);
   for (int f = 0; f < nfreq; ++f) {
     int* p = perm.data() + (size_t)f * n_tied;
-    for (int s = 0; s < n_tied; ++s) p[s] = s;
-    if (!dense_x) {
-      const double* uf = u + (size_t)f * n_tied;
-      std::stable_sort(p, p + n_tied, [&](int a, int b) {
-        long long ka = ((llrint(uf[a] * mx) % mx) + mx) % mx;
-        long long kb = ((llrint(uf[b] * mx) % mx) + mx) % mx;
-        return ka < kb;
-      });
+    if (dense_x) {
+      for (int s = 0; s < n_tied; ++s) p[s] = s;
+      continue;
     }
+    const double* uf = u + (size_t)f * n_tied;
+    std::fill(count.begin(), count.end(), 0);
+    for (int s = 0; s < n_tied; ++s) {
+      key[s] = (int)(((llrint(uf[s] * mx) % mx) + mx) % mx);
+      ++count[key[s] + 1];
+    }
+    for (int k = 0; k < mx; ++k) count[k + 1] += count[k];
+    for (int s = 0; s < n_tied; ++s) p[count[key[s]]++] = s;
   }
   // (re)allocate the tables of the path in use
   cudaFree(tt.wx);
@@ -306,12 +449,33 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
         tt.first, tt.cw);
     FFTBF_CUDA_TRY(cudaGetLastError());
   } else {
-    tied_table_kernel<<<blocks((int64_t)nuv * mx), threads, 0, st>>>(
-        nx, mx, mode_x, gx, tt.win_x.trunc, nfreq, n_tied, tt.duv, tt.perm, tt.wx);
-    FFTBF_CUDA_TRY(cudaGetLastError());
-    tied_table_kernel<<<blocks((int64_t)nuv * my), threads, 0, st>>>(
-        ny, my, mode_y, gy, tt.win_y.trunc, nfreq, n_tied, tt.duv + nuv, tt.perm, tt.wy);
-    FFTBF_CUDA_TRY(cudaGetLastError());
+    // per axis: the row kernels for the Dirichlet and (power-of-two M) windowed tables,
+    // else the per-weight kernel
+    auto axis_table = [&](int n, int M, int mode, const double* g, int trunc, const double* yy,
+                          float* out) -> int {
+      const int grid = (int)std::min<int64_t>((int64_t)nuv, (int64_t)tt_sms(st) * 4);
+      if (mode == 0 && M <= 4096) {
+        const size_t sm = sizeof(double2) * 2 * (size_t)M;
+        FFTBF_CUDA_TRY(cudaFuncSetAttribute(tied_dirichlet_table_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        tied_dirichlet_table_kernel<<<grid, threads, sm, st>>>(n, M, trunc, nfreq, n_tied, yy,
+                                                               tt.perm, out);
+      } else if (mode == 2 && M <= 4096 && (M & (M - 1)) == 0 && M >= 2 && n <= 2048) {
+        const size_t sm = sizeof(double2) * ((size_t)M / 2 + 2 * (size_t)M);
+        FFTBF_CUDA_TRY(cudaFuncSetAttribute(tied_window_table_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        tied_window_table_kernel<<<grid, threads, sm, st>>>(n, M, g, trunc, nfreq, n_tied, yy,
+                                                            tt.perm, out);
+      } else {
+        tied_table_kernel<<<blocks((int64_t)nuv * M), threads, 0, st>>>(n, M, mode, g, trunc, nfreq,
+                                                                        n_tied, yy, tt.perm, out);
+      }
+      FFTBF_CUDA_TRY(cudaGetLastError());
+      return FFTBF_OK;
+    };
+    int rc = axis_table(nx, mx, mode_x, gx, tt.win_x.trunc, tt.duv, tt.wx);
+    if (rc == FFTBF_OK) rc = axis_table(ny, my, mode_y, gy, tt.win_y.trunc, tt.duv + nuv, tt.wy);
+    if (rc != FFTBF_OK) return rc;
   }
   tt.built_version = tt.version;
   tt.n_tied = n_tied;
