@@ -19,8 +19,10 @@
 // the mantissa of 1024, weight x scale pre-rounded to FP16, the E-W butterflies in half2)
 // and the twiddle between the stages as a half2 complex multiply; this roughly halves the
 // CUDA-core instructions per snapshot at about 1.3x the FP16 rounding error.
-// A CTA (4 warps, 128 TMEM columns) processes the two polarisations of one time sample
-// (two snapshots) per iteration; four CTAs share an SM's 512 TMEM columns. Every wait on
+// A CTA (4 warps, 64 TMEM columns: stage 2 reuses the columns of stage 1 once they are
+// drained; the stage-1 operand likewise overlays the stage-2 operand in shared memory)
+// processes the two polarisations of one time sample (two snapshots) per iteration; five
+// CTAs per SM (registers and shared memory), 320 of the 512 TMEM columns. Every wait on
 // the tensor core is bounded by device time; on timeout the kernel records an error word
 // (FFTBF_ETIMEOUT at fftbf_plan_sync), frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -40,7 +42,8 @@ constexpr int A1_LBO = 128, A1_SBO = 512, A1_BYTES = 16 * 512;     // 128 rows x
 constexpr int A2_LBO = 144, A2_SBO = 592, A2_BYTES = 16 * 592;     // padded: conflict-free stores
 constexpr int B_LBO = 128, B_SBO = 512;
 constexpr int B1_BYTES = 8 * 512, B2_BYTES = 4 * 512;              // 64 and 32 rows x K 32
-constexpr uint32_t TMEM_COLS = 128;    // D1: cols 0-63, D2 (two snapshots): 64-95, 96-127
+constexpr uint32_t TMEM_COLS = 64;     // D1: cols 0-63; D2 (two snapshots, after D1 is
+                                       // drained): 0-31, 32-63
 constexpr uint64_t WAIT_NS = 1000000000ull;
 }  // namespace tcl
 
@@ -122,8 +125,10 @@ __host__ __device__ inline TcSmem tc_smem_layout(int nant) {
   TcSmem L;
   int o = 0;
   auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
-  L.a1 = take(tcl::A1_BYTES);
+  // A1 overlays the first bytes of A2: A1 is consumed by stage 1 before A2 is written,
+  // and A2 by stage 2 before the next A1 is written
   L.a2 = take(2 * tcl::A2_BYTES);
+  L.a1 = L.a2;
   L.b1 = take(tcl::B1_BYTES);
   L.b2 = take(tcl::B2_BYTES);
   L.tw = take(16 * 32 * 8);
@@ -146,7 +151,7 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
+__global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
@@ -318,13 +323,13 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
       const int sA = m >> 4, n2 = m & 15, s = sA >> 2, A = sA & 3;
       unsigned char* a2s = a2 + s * tcl::A2_BYTES;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t r[32];
-        tc::tmem_ld32(tbase + tlane + 32 * half, r);
+      for (int q = 0; q < 4; ++q) {
+        uint32_t r[16];
+        tc::tmem_ld16(tbase + tlane + 16 * q, r);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int k1 = 16 * half + j;
+        for (int j = 0; j < 8; ++j) {
+          const int k1 = 8 * q + j;
           uint32_t yv;
           if constexpr (!BF16) {
             const uint2 t = reinterpret_cast<const uint2*>(twsm)[k1 * 16 + n2];
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
         const uint32_t sa = tc::smem_u32(a2 + s * tcl::A2_BYTES);
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk)
-          tc::mma_f16(tbase + 64 + 32 * s,
+          tc::mma_f16(tbase + 32 * s,
                       tc::smem_desc(sa + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
                       tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id2, kk);
       }
@@ -363,13 +368,17 @@ __global__ void __launch_bounds__(tcl::NT, 4) beams_tc_kernel(const TcArgs ta) {
     // ---- drain stage 2: warp A, lane k1 squares X[k1 + 32 k2] and accumulates
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      uint32_t r[32];
-      tc::tmem_ld32(tbase + tlane + 64 + 32 * s, r);
-      tc::tmem_wait_ld();
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        const float re = __uint_as_float(r[2 * k2]), im = __uint_as_float(r[2 * k2 + 1]);
-        acc[k2] = fmaf(re, re, fmaf(im, im, acc[k2]));
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t r[16];
+        tc::tmem_ld16(tbase + tlane + 32 * s + 16 * hh, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k2 = 8 * hh + j;
+          const float re = __uint_as_float(r[2 * j]), im = __uint_as_float(r[2 * j + 1]);
+          acc[k2] = fmaf(re, re, fmaf(im, im, acc[k2]));
+        }
       }
     }
     tc::fence_before_sync();
@@ -766,16 +775,17 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const char* pipe = getenv("FFTBF_TC_PIPE");
   if (!(pipe && pipe[0] && pipe[0] != '0')) {
     const TcSmem L = tc_smem_layout(a.nx * a.ny);
-    // at most 4 CTAs of 128 TMEM columns per SM: keep a fifth from fitting
+    // at most 8 CTAs of 64 TMEM columns per SM: keep a ninth from fitting (registers and
+    // this shared memory hold it at 5 on the 4x256 lattice)
     size_t smem = (size_t)L.total;
-    if (smem < 46 * 1024) smem = 46 * 1024;
+    if (smem < 26 * 1024) smem = 26 * 1024;
     if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
     auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
-    int rc = tc_residency((const void*)kern, smem, tcl::NT, 4, &per_sm);
+    int rc = tc_residency((const void*)kern, smem, tcl::NT, 8, &per_sm);
     if (rc != FFTBF_OK) return rc;
     const int64_t grid = items < (int64_t)nsm * per_sm ? items : (int64_t)nsm * per_sm;
     kern<<<(unsigned)grid, tcl::NT, smem, st>>>(ta);
