@@ -212,3 +212,27 @@ def test_tied_rejects_off_grid_pointing():
         with pytest.raises(fb.FftbfError) as e:
             fb.tied_beams(plan, P, 1, 1, np.array([0.3]), np.array([0.5]), out)
         assert e.value.code == -1 and "off the FFT-beam grid" in str(e.value)
+
+
+@pytest.mark.parametrize("shape,prec", [((4, 256, 4, 512, 2, 2, 32, 16), "fp32"),
+                                        ((3, 128, 3, 256, 2, 2, 32, 16), "fp32"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16")])
+def test_misaligned_voltages_give_identical_beams(shape, prec):
+    """A voltage pointer off the 16-byte boundary is accepted (staged byte by byte instead
+    of with 16-byte copies) and gives bit-identical beams."""
+    nx, ny, mx, my, npol, nfreq, T, n_int = shape
+    v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=77)
+    flat = torch.from_numpy(np.ascontiguousarray(v).reshape(-1))
+    base = torch.zeros(flat.numel() + 16, dtype=torch.uint8, device="cuda")
+    outs = []
+    for off in (0, 3):
+        base[off:off + flat.numel()].copy_(flat)
+        out = torch.full((T // n_int, nfreq, mx, my), float("nan"), device="cuda")
+        with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
+            if prec == "tc_fp16":
+                fb.plan_set_precision(plan, fb.PREC_TC_FP16)
+            fb.execute(plan, base[off:off + flat.numel()], T, out)
+            fb.plan_sync(plan)
+        outs.append(out.cpu().numpy())
+    assert np.all(np.isfinite(outs[0]))
+    assert np.array_equal(outs[0], outs[1])
