@@ -90,7 +90,7 @@ __device__ __forceinline__ void move(int M, int* ih, float* fr, float dyM) {
   *fr = f;
 }
 
-__global__ void __launch_bounds__(32 * kLocWarps) localise_kernel(
+__global__ void __launch_bounds__(32 * kLocWarps, 4) localise_kernel(
     const float* __restrict__ P, float* __restrict__ out, int64_t items, LocAxis axx,
     LocAxis axy, int n_iter, int taps_x, int taps_y, int vec4) {
   __shared__ float sw[kLocWarps][4][kLocTaps];         // wx, dwx, wy, dwy of the taps
@@ -230,7 +230,7 @@ extern "C" int fftbf_localise(fftbf_plan* p, const float* beams_dev, int64_t n_w
   cudaGetDevice(&prev);
   if (prev != p->device) cudaSetDevice(p->device);
   const int64_t items = n_windows * p->nfreq;
-  const int64_t blocks = std::min<int64_t>((items + kLocWarps - 1) / kLocWarps, (int64_t)p->nsm * 8);
+  const int64_t blocks = std::min<int64_t>((items + kLocWarps - 1) / kLocWarps, (int64_t)p->nsm * 4);
   localise_kernel<<<(unsigned)blocks, 32 * kLocWarps, 0, static_cast<cudaStream_t>(stream)>>>(
       beams_dev, out_dev, items, ax, ay, n_iter, std::min(n_taps, p->mx), std::min(n_taps, p->my),
       vec4);

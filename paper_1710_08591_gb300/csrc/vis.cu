@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(256) stacked_vis_kernel(const float* __restric
 // complex transform z = P_a + i P_b, Z[k] = sum_B z_B exp(+2 pi i k B / My) (radix-2
 // Stockham in shared memory), and the rows separate by Hermitian symmetry,
 //   X_a[k] = (Z[k] + conj Z[My-k]) / 2,   X_b[k] = (Z[k] - conj Z[My-k]) / 2i,
-// with V~_delta = X[delta] / My for delta >= 0 and conj(X[-delta]) / My below. The E-W step
-// (when Mx >= 2nx - 1) is the direct one above.
+// with V~_delta = X[delta] / My for delta >= 0 and conj(X[-delta]) / My below. All row
+// pairs of a (window, channel) go through the same stage loop (one barrier per stage for
+// the whole tile). The E-W step (when Mx >= 2nx - 1) is the direct one above.
 __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __restrict__ P,
                                                               float2* __restrict__ out,
                                                               const float2* __restrict__ tw_y,
@@ -103,10 +104,12 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
                                                               int mx, int my, int inv_x) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int half = my >> 1, dy_n = 2 * ny - 1, dx_n = inv_x ? 2 * nx - 1 : mx;
+  const int np = (mx + 1) >> 1;                    // row pairs, transformed together
+  const int lh = __ffs(half) - 1, lm = lh + 1;     // log2(My/2), log2(My)
   float2* twp = reinterpret_cast<float2*>(smem);   // [My/2] exp(+2 pi i k / My)
-  float2* buf0 = twp + half;                       // [My]
-  float2* buf1 = buf0 + my;                        // [My]
-  float2* q = buf1 + my;                           // [Mx][dy_n] when inverting E-W
+  float2* buf0 = twp + half;                       // [np][My]
+  float2* buf1 = buf0 + np * my;                   // [np][My]
+  float2* q = buf1 + np * my;                      // [Mx][dy_n] when inverting E-W
   float2* txs = q + (inv_x ? mx * dy_n : 0);       // [Mx] exp(+2 pi i k / Mx)
   for (int i = threadIdx.x; i < half; i += blockDim.x) {
     const float2 t = tw_y[i];
@@ -122,41 +125,43 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
     const float* tile = P + item * (int64_t)(mx * my);
     float2* dst = out + item * (int64_t)(dx_n * dy_n);
-    for (int r = 0; r < mx; r += 2) {
-      __syncthreads();
-      const float* ra = tile + r * my;
-      const bool two = r + 1 < mx;
-      for (int B = threadIdx.x; B < my; B += blockDim.x)
-        buf0[B] = make_float2(ra[B], two ? ra[my + B] : 0.f);
-      __syncthreads();
-      float2* src = buf0;
-      float2* dsb = buf1;
-      for (int ns = 1; ns < my; ns <<= 1) {
-        for (int j = threadIdx.x; j < half; j += blockDim.x) {
-          const int k = j & (ns - 1);
-          const float2 w = twp[k * (half / ns)];
-          const float2 a = src[j], b0 = src[j + half];
-          const float2 b = make_float2(b0.x * w.x - b0.y * w.y, b0.x * w.y + b0.y * w.x);
-          const int d = ((j - k) << 1) + k;
-          dsb[d] = make_float2(a.x + b.x, a.y + b.y);
-          dsb[d + ns] = make_float2(a.x - b.x, a.y - b.y);
-        }
-        __syncthreads();
-        float2* t = src; src = dsb; dsb = t;
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * my; i += blockDim.x) {
+      const int r = 2 * (i >> lm), B = i & (my - 1);
+      buf0[i] = make_float2(tile[r * my + B], r + 1 < mx ? tile[(r + 1) * my + B] : 0.f);
+    }
+    __syncthreads();
+    float2* src = buf0;
+    float2* dsb = buf1;
+    for (int ns = 1, ls = 0; ns < my; ns <<= 1, ++ls) {
+      for (int jj = threadIdx.x; jj < np * half; jj += blockDim.x) {
+        const int pr = jj >> lh, j = jj & (half - 1);
+        const float2* sp = src + pr * my;
+        float2* dp = dsb + pr * my;
+        const int k = j & (ns - 1);
+        const float2 w = twp[k << (lh - ls)];
+        const float2 a = sp[j], b0 = sp[j + half];
+        const float2 b = make_float2(b0.x * w.x - b0.y * w.y, b0.x * w.y + b0.y * w.x);
+        const int d = ((j - k) << 1) + k;
+        dp[d] = make_float2(a.x + b.x, a.y + b.y);
+        dp[d + ns] = make_float2(a.x - b.x, a.y - b.y);
       }
-      for (int o = threadIdx.x; o < 2 * dy_n; o += blockDim.x) {
-        const int row = o >= dy_n, d = o - row * dy_n;
-        if (r + row >= mx) continue;
-        const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
-        const float2 zk = src[k], zm = src[(my - k) & (my - 1)];
-        float2 x = row == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
-                            : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        if (lag < 0) x.y = -x.y;
-        x.x *= iny;
-        x.y *= iny;
-        if (inv_x) q[(r + row) * dy_n + d] = x;
-        else dst[(r + row) * dy_n + d] = x;
-      }
+      __syncthreads();
+      float2* t = src; src = dsb; dsb = t;
+    }
+    for (int o = threadIdx.x; o < mx * dy_n; o += blockDim.x) {
+      const int A = o / dy_n, d = o - A * dy_n;
+      const int row = A & 1;
+      const float2* z = src + (A >> 1) * my;
+      const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
+      const float2 zk = z[k], zm = z[(my - k) & (my - 1)];
+      float2 x = row == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
+                          : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      if (lag < 0) x.y = -x.y;
+      x.x *= iny;
+      x.y *= iny;
+      if (inv_x) q[o] = x;
+      else dst[o] = x;
     }
     if (inv_x) {
       __syncthreads();
@@ -203,7 +208,7 @@ int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_
   fftbf_stacked_shape(p, &dx, &dy);
   // FFT route: N-S invertible and My a power of two (>= 2)
   const bool fft = inv_y && p->my >= 2 && (p->my & (p->my - 1)) == 0;
-  const size_t smem_fft = sizeof(float2) * ((size_t)p->my / 2 + 2 * (size_t)p->my +
+  const size_t smem_fft = sizeof(float2) * ((size_t)p->my / 2 + 2 * (size_t)((p->mx + 1) / 2) * p->my +
                                             (inv_x ? (size_t)p->mx * dy + p->mx : 0));
   const size_t smem = sizeof(float) * (((size_t)p->mx * p->my + 1) & ~(size_t)1) +
                       sizeof(float2) * ((size_t)p->my + p->mx + (size_t)p->mx * dy);
