@@ -348,6 +348,7 @@ static float time_candidate(fftbf_batch* bb, const fftbf_plan* p, int variant, i
 extern "C" {
 
 fftbf_batch* fftbf_batch_create(fftbf_plan* const* plans, int n) {
+  NvtxRange nvtx("fftbf_batch_create (autotune)");
   if (!plans || n < 1 || n > bt::kMaxJobs) {
     set_error(FFTBF_EINVAL, "need 1..%d plans", bt::kMaxJobs);
     return nullptr;
@@ -472,6 +473,7 @@ fftbf_batch* fftbf_batch_create(fftbf_plan* const* plans, int n) {
 
 int fftbf_batch_execute(fftbf_batch* bb, const uint8_t* const* volts_dev, int64_t T,
                         float* const* beams_dev, void* stream) {
+  NvtxRange nvtx("fftbf_batch_execute");
   if (!bb) return set_error(FFTBF_EINVAL, "null batch");
   if (!volts_dev || !beams_dev) return set_error(FFTBF_EINVAL, "null pointer array");
   const int n = (int)bb->plans.size();

@@ -154,6 +154,7 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
 }
 
 int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, void* stream) {
+  NvtxRange nvtx("fftbf_execute");
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   if (T < 0 || T % p->n_int != 0)
     return set_error(FFTBF_EINVAL, "T = %lld is not a non-negative multiple of n_int = %d",
@@ -198,6 +199,7 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
 
 int fftbf_tied_beams(fftbf_plan* p, const float* beams, int64_t n_windows, int n_tied,
                      const double* u, const double* v, float* tied, void* stream) {
+  NvtxRange nvtx("fftbf_tied_beams");
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   if (n_windows < 0 || n_tied < 1)
     return set_error(FFTBF_EINVAL, "need n_windows >= 0 and n_tied >= 1");

@@ -49,6 +49,7 @@ using namespace fftbf;
 extern "C" int fftbf_execute_host(fftbf_plan* p, const uint8_t* volts_h, int64_t T,
                                   float* beams_h, int n_tied, const double* u,
                                   const double* v, float* tied_h, void* stream) {
+  NvtxRange nvtx("fftbf_execute_host");
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   if (T < 0 || T % p->n_int != 0)
     return set_error(FFTBF_EINVAL, "T = %lld is not a non-negative multiple of n_int = %d",

@@ -9,7 +9,17 @@
 
 #include "fftbf.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace fftbf {
+
+// NVTX range over an entry point (header-only NVTX v3: no cost unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Thread-local error message plus status code.
 int set_error(int code, const char* fmt, ...);

@@ -207,6 +207,7 @@ using namespace fftbf;
 
 extern "C" int fftbf_localise(fftbf_plan* p, const float* beams_dev, int64_t n_windows,
                               int n_iter, int n_taps, float* out_dev, void* stream) {
+  NvtxRange nvtx("fftbf_localise");
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   if (n_windows < 0 || n_iter < 0 || n_taps < 1 || n_taps > kLocTaps)
     return set_error(FFTBF_EINVAL, "need n_windows >= 0, n_iter >= 0, 1 <= n_taps <= %d",

@@ -117,6 +117,7 @@ void run_scheduler(fftbf_server* sv) {
     // ---- launch a tick over everything staged
     Tick& tk = sv->ticks[sv->next_tick];
     if (!sv->staged.empty() && !tk.busy) {
+      NvtxRange nvtx("serve tick");
       const int n = (int)std::min<size_t>(sv->staged.size(), kJobsPerTick);
       tk.frames.assign(sv->staged.begin(), sv->staged.begin() + n);
       sv->staged.erase(sv->staged.begin(), sv->staged.begin() + n);

@@ -199,6 +199,7 @@ int fftbf_stacked_shape(const fftbf_plan* p, int* dx, int* dy) {
 
 int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_windows,
                                float* vis_dev, void* stream) {
+  NvtxRange nvtx("fftbf_stacked_visibilities");
   if (!p) return set_error(FFTBF_EINVAL, "null plan");
   if (n_windows < 0) return set_error(FFTBF_EINVAL, "n_windows < 0");
   if (n_windows == 0) return FFTBF_OK;
