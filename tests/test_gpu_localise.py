@@ -44,3 +44,36 @@ def test_localise_matches_oracle(shape):
     # and the estimate sits near the source (quantisation and noise limit the accuracy)
     if my >= 2 * ny - 1:
         assert np.abs(((got[..., 1] - 0.6021) + 0.5) % 1.0 - 0.5).max() < 0.2 / my
+
+
+@pytest.mark.parametrize("n_iter,n_taps", [(0, 10), (3, 33), (4, 64)])
+def test_localise_taps_and_iterations(n_iter, n_taps):
+    """More taps than lanes (33, 64: the maximum), no Newton step (the argmax beam), and an
+    odd fitted E-W pad."""
+    nx, ny, mx, my, npol, nfreq, T, n_int = 3, 32, 7, 64, 2, 2, 32, 16
+    v8 = synth.volts(T, nfreq, npol, nx, ny, seed=41, sigma=1.0, sources=[(0.61, 0.27, 3.0)])
+    dv = torch.from_numpy(v8.reshape(-1)).cuda()
+    nwin = T // n_int
+    P = torch.empty((nwin, nfreq, mx, my), device="cuda")
+    out = torch.full((nwin, nfreq, 3), float("nan"), device="cuda")
+    with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int) as plan:
+        fb.execute(plan, dv, T, P)
+        fb.localise(plan, P, nwin, out, n_iter=n_iter, n_taps=n_taps)
+        fb.plan_sync(plan)
+    got = out.cpu().numpy()
+    ref = oracle.localise(oracle_beams(v8, None, nx, ny, mx, my, npol, nfreq, n_int), nx, ny,
+                          n_iter=n_iter, n_taps=n_taps)
+    for c in (0, 1):
+        d = np.abs(((got[..., c] - ref[..., c]) + 0.5) % 1.0 - 0.5)
+        assert d.max() < 2e-6, (c, d.max())
+    assert np.allclose(got[..., 2], ref[..., 2], rtol=1e-5)
+
+
+def test_localise_rejects_bad_taps():
+    with fb.plan_create(2, 8, 2, 16, 1, 1, 4) as plan:
+        P = torch.zeros((1, 1, 2, 16), device="cuda")
+        out = torch.zeros((1, 1, 3), device="cuda")
+        for bad in (0, 65):
+            with pytest.raises(fb.FftbfError) as e:
+                fb.localise(plan, P, 1, out, n_iter=2, n_taps=bad)
+            assert e.value.code == -1

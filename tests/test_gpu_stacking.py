@@ -20,7 +20,9 @@ def _lib():
 
 @pytest.mark.parametrize("shape", [(3, 8, 5, 16, 2, 3, 32, 16),      # both axes invertible
                                    (4, 256, 4, 512, 2, 2, 384, 384),  # E-W kept, N-S lags
-                                   (2, 16, 2, 32, 1, 8, 64, 16)])     # the tiny workload
+                                   (2, 16, 2, 32, 1, 8, 64, 16),      # the tiny workload
+                                   (3, 40, 3, 128, 2, 2, 32, 16),     # odd E-W rows: a row paired with zeros
+                                   (2, 10, 3, 24, 1, 2, 16, 8)])      # N-S pad not a power of two: direct route
 def test_stacked_visibilities_match_oracle(shape):
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v8, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="random", seed=90)
