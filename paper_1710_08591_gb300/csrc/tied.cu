@@ -261,6 +261,137 @@ __global__ void __launch_bounds__(256) tied_compact_kernel(const float* __restri
 
 constexpr int TS = 64, TJ = 64, TK = 16;
 
+// Regridding GEMM with 128 pointings x 128 windows per CTA (256 threads, 8 x 8 outputs
+// each: rows 4 tm .. + 3 and 64 + 4 tm .. + 3, the same for columns, so the float4 reads
+// of a k-step fall in distinct banks), K steps of 16 FFT beams double-buffered through
+// registers (the next step's global loads are in flight while this one is multiplied).
+// The K loop runs over the E-W beams A that some pointing of the tile weights (one or two
+// for a one-hot E-W axis, the pointings being sorted by it) and the N-S beams B:
+//   out[j, f, perm(s)] = sum_A sum_B wx[f, s, A] wy[f, s, B] P[j, f, A, B].
+constexpr int GM = 128, GN = 128, GK = 16;
+#ifndef FFTBF_TIED_MIN_BLOCKS
+#define FFTBF_TIED_MIN_BLOCKS 2   // CTAs per SM the register budget of the GEMM targets
+#endif
+
+__global__ void __launch_bounds__(256, FFTBF_TIED_MIN_BLOCKS) tied_gemm128_kernel(const float* __restrict__ P,
+                                                              const float* __restrict__ wx,
+                                                              const float* __restrict__ wy,
+                                                              const int* __restrict__ perm,
+                                                              float* __restrict__ out,
+                                                              int64_t nwin, int nfreq, int n_tied,
+                                                              int mx, int my) {
+  __shared__ __align__(16) float As[2][GK][GM + 4];
+  __shared__ __align__(16) float Bs[2][GK][GN + 4];
+  __shared__ unsigned long long s_active;
+  const int f = blockIdx.z;
+  const int s0 = blockIdx.x * GM;
+  const int64_t j0 = (int64_t)blockIdx.y * GN;
+  const int tid = threadIdx.x, tm = tid >> 4, tn = tid & 15;
+  const int64_t fs0 = (int64_t)f * n_tied;
+  const int64_t prow = (int64_t)nfreq * mx * my;
+  // E-W beams used by this tile's pointings (mx <= 64)
+  if (tid == 0) s_active = 0ull;
+  __syncthreads();
+  for (int i = tid; i < GM * mx; i += blockDim.x) {
+    const int r = i / mx, A = i - (i / mx) * mx;
+    if (s0 + r < n_tied && wx[(fs0 + s0 + r) * mx + A] != 0.f) atomicOr(&s_active, 1ull << A);
+  }
+  __syncthreads();
+  const unsigned long long active = s_active;
+  const int kb = (my + GK - 1) / GK;
+  // load mapping: row (pointing / window) = tid >> 1, eight consecutive k from (tid & 1) * 8
+  // (two float4 when the rows are 16-byte aligned)
+  const int lr = tid >> 1, lk = (tid & 1) * 8;
+  const int gs = s0 + lr;
+  const int64_t gj = j0 + lr;
+  const bool vec = (my & 3) == 0;
+  float ra[8], rb[8];
+  auto load = [&](int A, int b0) {
+    const float w = gs < n_tied ? wx[(fs0 + gs) * mx + A] : 0.f;
+    const float* wrow = wy + (fs0 + gs) * my + b0 + lk;
+    const float* prow_p = P + gj * prow + (int64_t)f * mx * my + (int64_t)A * my + b0 + lk;
+    const bool rin = gs < n_tied, pin = gj < nwin;
+    if (vec && b0 + lk + 8 <= my) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 a = rin ? *reinterpret_cast<const float4*>(wrow + 4 * h) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 p = pin ? *reinterpret_cast<const float4*>(prow_p + 4 * h) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ra[4 * h] = w * a.x; ra[4 * h + 1] = w * a.y; ra[4 * h + 2] = w * a.z; ra[4 * h + 3] = w * a.w;
+        rb[4 * h] = p.x; rb[4 * h + 1] = p.y; rb[4 * h + 2] = p.z; rb[4 * h + 3] = p.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool kin = b0 + lk + i < my;
+        ra[i] = (rin && kin) ? w * wrow[i] : 0.f;
+        rb[i] = (pin && kin) ? prow_p[i] : 0.f;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      As[buf][lk + i][lr] = ra[i];
+      Bs[buf][lk + i][lr] = rb[i];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[i][q] = 0.f;
+  // the (A, b0) steps in order
+  int A = 0;
+  while (A < mx && !((active >> A) & 1ull)) ++A;
+  if (A < mx) {
+    int b = 0, buf = 0;
+    load(A, 0);
+    store(0);
+    __syncthreads();
+    while (true) {
+      // next step
+      int nA = A, nb = b + 1;
+      if (nb == kb) {
+        nb = 0;
+        ++nA;
+        while (nA < mx && !((active >> nA) & 1ull)) ++nA;
+      }
+      const bool more = nA < mx;
+      if (more) load(nA, nb * GK);
+#pragma unroll
+      for (int k = 0; k < GK; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][4 * tm]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + 4 * tm]);
+        const float4 b0v = *reinterpret_cast<const float4*>(&Bs[buf][k][4 * tn]);
+        const float4 b1v = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + 4 * tn]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0v.x, b0v.y, b0v.z, b0v.w, b1v.x, b1v.y, b1v.z, b1v.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[i][q] = fmaf(av[i], bv[q], acc[i][q]);
+      }
+      if (!more) break;
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+      A = nA;
+      b = nb;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int s = s0 + (i < 4 ? 4 * tm + i : 64 + 4 * tm + i - 4);
+    if (s >= n_tied) continue;
+    const int dst = perm[fs0 + s];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t j = j0 + (q < 4 ? 4 * tn + q : 64 + 4 * tn + q - 4);
+      if (j < nwin) out[(j * nfreq + f) * (int64_t)n_tied + dst] = acc[i][q];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) tied_gemm_kernel(const float* __restrict__ P,
                                                          const float* __restrict__ wx,
                                                          const float* __restrict__ wy,
@@ -490,6 +621,16 @@ int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfre
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
     tied_compact_kernel<<<blocks, 256, 0, st>>>(beams, tt.first, tt.cw, out, nwin, nfreq,
                                                 tt.n_tied, mx, my, tt.kx, tt.ky);
+    FFTBF_CUDA_TRY(cudaGetLastError());
+    return FFTBF_OK;
+  }
+  if (mx <= 64 && nwin >= 64) {
+    const int64_t jt = (nwin + GN - 1) / GN;
+    if (jt > 65535 || nfreq > 65535)
+      return set_error(FFTBF_EUNSUPPORTED, "tied beams: too many windows or channels per call");
+    dim3 grid((tt.n_tied + GM - 1) / GM, (unsigned)jt, nfreq);
+    tied_gemm128_kernel<<<grid, 256, 0, st>>>(beams, tt.wx, tt.wy, tt.perm, out, nwin, nfreq,
+                                              tt.n_tied, mx, my);
     FFTBF_CUDA_TRY(cudaGetLastError());
     return FFTBF_OK;
   }
