@@ -7,7 +7,7 @@
 // E-W step (if any) combines the Mx rows. FP32 sums of FP32 twiddles (from FP64).
 #include <cuda_runtime.h>
 
-#include "internal.cuh"
+#include "beam_fp32.cuh"
 
 namespace fftbf {
 
@@ -96,7 +96,9 @@ __global__ void __launch_bounds__(256) stacked_vis_kernel(const float* __restric
 //   X_a[k] = (Z[k] + conj Z[My-k]) / 2,   X_b[k] = (Z[k] - conj Z[My-k]) / 2i,
 // with V~_delta = X[delta] / My for delta >= 0 and conj(X[-delta]) / My below. All row
 // pairs of a (window, channel) go through the same stage loop (one barrier per stage for
-// the whole tile). The E-W step (when Mx >= 2nx - 1) is the direct one above.
+// the whole tile), whose first stage reads the raw rows; the next (window, channel) tile
+// is fetched with cp.async meanwhile. The E-W step (when Mx >= 2nx - 1) is the direct one
+// above.
 __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __restrict__ P,
                                                               float2* __restrict__ out,
                                                               const float2* __restrict__ tw_y,
@@ -105,8 +107,10 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
   extern __shared__ __align__(16) unsigned char smem[];
   const int half = my >> 1, dy_n = 2 * ny - 1, dx_n = inv_x ? 2 * nx - 1 : mx;
   const int np = (mx + 1) >> 1;                    // row pairs, transformed together
-  const int lh = __ffs(half) - 1, lm = lh + 1;     // log2(My/2), log2(My)
-  float2* twp = reinterpret_cast<float2*>(smem);   // [My/2] exp(+2 pi i k / My)
+  const int lh = __ffs(half) - 1;                  // log2(My/2)
+  const int tsz = mx * my;                         // floats per beam tile
+  float* tiles = reinterpret_cast<float*>(smem);   // [2][Mx * My] raw tiles, next one in flight
+  float2* twp = reinterpret_cast<float2*>(tiles + 2 * ((tsz + 3) & ~3));   // [My/2] exp(+2 pi i k / My)
   float2* buf0 = twp + half;                       // [np][My]
   float2* buf1 = buf0 + np * my;                   // [np][My]
   float2* q = buf1 + np * my;                      // [Mx][dy_n] when inverting E-W
@@ -122,18 +126,44 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
       txs[i] = make_float2((float)c, (float)s);
     }
   const float iny = 1.0f / (float)my, inx = 1.0f / (float)mx;
+  // tiles are fetched with 16-byte cp.async when they start on 16-byte boundaries
+  const bool vec = (tsz & 3) == 0 && (reinterpret_cast<uintptr_t>(P) & 15) == 0;
+  auto fetch = [&](int64_t itm, float* dst) {
+    if (itm >= nitems) return;
+    const float* src = P + itm * (int64_t)tsz;
+    if (vec) {
+      for (int i = threadIdx.x; i < (tsz >> 2); i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+    } else {
+      for (int i = threadIdx.x; i < tsz; i += blockDim.x) dst[i] = src[i];
+    }
+  };
+  int cur = 0;
+  fetch(blockIdx.x, tiles);
+  cp_async_commit();
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const float* tile = P + item * (int64_t)(mx * my);
     float2* dst = out + item * (int64_t)(dx_n * dy_n);
-    __syncthreads();
-    for (int i = threadIdx.x; i < np * my; i += blockDim.x) {
-      const int r = 2 * (i >> lm), B = i & (my - 1);
-      buf0[i] = make_float2(tile[r * my + B], r + 1 < mx ? tile[(r + 1) * my + B] : 0.f);
+    __syncthreads();                               // the other tile buffer is free again
+    fetch(item + gridDim.x, tiles + (cur ^ 1) * ((tsz + 3) & ~3));
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();                               // this item's tile is in shared memory
+    const float* tile = tiles + cur * ((tsz + 3) & ~3);
+    // first stage (Ns = 1, unit twiddle) straight from the rows: z = P_a + i P_b
+    for (int jj = threadIdx.x; jj < np * half; jj += blockDim.x) {
+      const int pr = jj >> lh, j = jj & (half - 1);
+      const int r = 2 * pr;
+      const float* ra = tile + r * my;
+      const bool two = r + 1 < mx;
+      const float2 a = make_float2(ra[j], two ? ra[my + j] : 0.f);
+      const float2 b = make_float2(ra[j + half], two ? ra[my + j + half] : 0.f);
+      float2* dp = buf0 + pr * my;
+      dp[2 * j] = make_float2(a.x + b.x, a.y + b.y);
+      dp[2 * j + 1] = make_float2(a.x - b.x, a.y - b.y);
     }
     __syncthreads();
     float2* src = buf0;
     float2* dsb = buf1;
-    for (int ns = 1, ls = 0; ns < my; ns <<= 1, ++ls) {
+    for (int ns = 2, ls = 1; ns < my; ns <<= 1, ++ls) {
       for (int jj = threadIdx.x; jj < np * half; jj += blockDim.x) {
         const int pr = jj >> lh, j = jj & (half - 1);
         const float2* sp = src + pr * my;
@@ -149,19 +179,20 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
       __syncthreads();
       float2* t = src; src = dsb; dsb = t;
     }
-    for (int o = threadIdx.x; o < mx * dy_n; o += blockDim.x) {
-      const int A = o / dy_n, d = o - A * dy_n;
+    for (int A = 0; A < mx; ++A) {
       const int row = A & 1;
       const float2* z = src + (A >> 1) * my;
-      const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
-      const float2 zk = z[k], zm = z[(my - k) & (my - 1)];
-      float2 x = row == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
-                          : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-      if (lag < 0) x.y = -x.y;
-      x.x *= iny;
-      x.y *= iny;
-      if (inv_x) q[o] = x;
-      else dst[o] = x;
+      for (int d = threadIdx.x; d < dy_n; d += blockDim.x) {
+        const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
+        const float2 zk = z[k], zm = z[(my - k) & (my - 1)];
+        float2 x = row == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
+                            : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        if (lag < 0) x.y = -x.y;
+        x.x *= iny;
+        x.y *= iny;
+        if (inv_x) q[A * dy_n + d] = x;
+        else dst[A * dy_n + d] = x;
+      }
     }
     if (inv_x) {
       __syncthreads();
@@ -181,7 +212,9 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
         dst[o] = make_float2(v.x * inx, v.y * inx);
       }
     }
+    cur ^= 1;
   }
+  cp_async_wait<0>();
 }
 
 }  // namespace fftbf
@@ -209,7 +242,8 @@ int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_
   fftbf_stacked_shape(p, &dx, &dy);
   // FFT route: N-S invertible and My a power of two (>= 2)
   const bool fft = inv_y && p->my >= 2 && (p->my & (p->my - 1)) == 0;
-  const size_t smem_fft = sizeof(float2) * ((size_t)p->my / 2 + 2 * (size_t)((p->mx + 1) / 2) * p->my +
+  const size_t smem_fft = sizeof(float) * 2 * (((size_t)p->mx * p->my + 3) & ~(size_t)3) +
+                          sizeof(float2) * ((size_t)p->my / 2 + 2 * (size_t)((p->mx + 1) / 2) * p->my +
                                             (inv_x ? (size_t)p->mx * dy + p->mx : 0));
   const size_t smem = sizeof(float) * (((size_t)p->mx * p->my + 1) & ~(size_t)1) +
                       sizeof(float2) * ((size_t)p->my + p->mx + (size_t)p->mx * dy);
