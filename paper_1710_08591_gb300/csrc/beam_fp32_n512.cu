@@ -24,14 +24,17 @@ namespace n512 {
 constexpr int kRegion = 32 * 17;   // float2 slots per transform region (X1 tile, padded)
 }
 
+#ifndef FFTBF_N512_NW
+#define FFTBF_N512_NW 4           // warps per CTA for E-W sizes up to 4 (snapshots = NW / MX)
+#endif
 #ifndef FFTBF_N512_MIN_BLOCKS
-#define FFTBF_N512_MIN_BLOCKS 6   // 4-warp CTAs per SM the register budget targets (80 regs)
+#define FFTBF_N512_MIN_BLOCKS (24 / FFTBF_N512_NW)   // CTAs per SM the register budget targets
 #endif
 
 template <int MX>
-__global__ void __launch_bounds__((MX > 4 ? MX : 4) * 32, MX > 4 ? 2 : FFTBF_N512_MIN_BLOCKS)
+__global__ void __launch_bounds__((MX > 4 ? MX : FFTBF_N512_NW) * 32, MX > 4 ? 2 : FFTBF_N512_MIN_BLOCKS)
 beams_fp32_n512_kernel(const BeamArgs a) {
-  constexpr int NW = MX > 4 ? MX : 4;       // warps per CTA = transforms per iteration
+  constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;   // warps per CTA = transforms per iteration
   constexpr int S = NW / MX;                // snapshots per iteration
   constexpr int NT = NW * 32;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -200,7 +203,7 @@ static size_t n512_smem_bytes(const BeamArgs& a, int S, int NW) {
 
 template <int MX>
 static int launch_n512_mx(const BeamArgs& a, int nsm, cudaStream_t st) {
-  constexpr int NW = MX > 4 ? MX : 4;
+  constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;
   constexpr int S = NW / MX;
   const size_t smem = n512_smem_bytes(a, S, NW);
   auto kern = beams_fp32_n512_kernel<MX>;
@@ -220,7 +223,8 @@ static int launch_n512_mx(const BeamArgs& a, int nsm, cudaStream_t st) {
 bool fp32_n512_supported(const BeamArgs& a) {
   const bool mx_ok = a.mx == 1 || a.mx == 2 || a.mx == 4 || a.mx == 8;
   return mx_ok && a.my == 512 && a.nyf <= 256 &&
-         n512_smem_bytes(a, a.mx > 4 ? 1 : 4 / a.mx, a.mx > 4 ? a.mx : 4) <= 200 * 1024;
+         n512_smem_bytes(a, a.mx > 4 ? 1 : FFTBF_N512_NW / a.mx, a.mx > 4 ? a.mx : FFTBF_N512_NW) <=
+             200 * 1024;
 }
 
 int launch_beams_fp32_n512(const BeamArgs& a, int nsm, cudaStream_t st) {
