@@ -91,7 +91,24 @@ __device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* 
           Dft<MX>::run(z);
         }
       }
-      if (!a.ew_dft) {
+      bool done = false;
+      if constexpr (MX == 3) {
+        if (a.nx == 3) {
+          // 3-point DFT: X_{1,2} = z0 - (z1 + z2)/2 -/+ i (sqrt(3)/2)(z1 - z2)
+          const float2 z0 = cmul(wsm[iy], unpack_byte(rs[iy]));
+          const float2 z1 = cmul(wsm[a.ny + iy], unpack_byte(rs[a.ny + iy]));
+          const float2 z2 = cmul(wsm[2 * a.ny + iy], unpack_byte(rs[2 * a.ny + iy]));
+          const float2 sm = cadd(z1, z2), df = csub(z1, z2);
+          const float h3 = 0.86602540378443865f;
+          const float2 m = make_float2(z0.x - 0.5f * sm.x, z0.y - 0.5f * sm.y);
+          const float2 t = make_float2(h3 * df.y, -h3 * df.x);
+          z[0] = cadd(z0, sm);
+          z[1] = cadd(m, t);
+          z[2] = csub(m, t);
+          done = true;
+        }
+      }
+      if (!a.ew_dft && !done) {
         for (int ix = 0; ix < a.nx; ++ix) {
           const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
 #pragma unroll
