@@ -235,7 +235,8 @@ def run_ours(args, rank, world, local_rank):
     tied = torch.empty((nwin, nfreq, n_tied), device=dev)
     plan = fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w)
     if args.form != "fp32":
-        fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16}[args.form])
+        fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16,
+                                     "tc_fp16x3": fb.PREC_TC_FP16X3}[args.form])
     stream = torch.cuda.current_stream(dev)
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(ncall)] for _ in range(args.steps)]
@@ -340,7 +341,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- the tensor-core forms on the same workload (same step, fewer timed steps)
     forms = {"fp32": {"value": value, "ms_per_step": ms_step}}
     if not args.no_forms and args.form == "fp32":
-        for form, prec in (("tc_fp16", fb.PREC_TC_FP16), ("tc_bf16", fb.PREC_TC_BF16)):
+        for form, prec in (("tc_fp16", fb.PREC_TC_FP16), ("tc_bf16", fb.PREC_TC_BF16),
+                           ("tc_fp16x3", fb.PREC_TC_FP16X3)):
             fplan = fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w)
             fb.plan_set_precision(fplan, prec)
 
@@ -622,7 +624,8 @@ def run_profile_case(args):
     tied = torch.empty((T // n_int, nfreq, n_tied), device="cuda")
     with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
         if args.form != "fp32":
-            fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16}[args.form])
+            fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16,
+                                     "tc_fp16x3": fb.PREC_TC_FP16X3}[args.form])
         for _ in range(3):
             fb.execute(plan, dvol, T, beams)
         fb.tied_beams(plan, beams, T // n_int, n_tied, u, v, tied)
@@ -637,7 +640,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp32", "tc_fp16", "tc_bf16"], default="fp32")
+    ap.add_argument("--form", choices=["fp32", "tc_fp16", "tc_bf16", "tc_fp16x3"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["chime", "batched"], default="chime")

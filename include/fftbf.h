@@ -56,7 +56,9 @@ enum fftbf_status {
 enum fftbf_precision {
   FFTBF_PREC_FP32 = 0,    /* FP32 CUDA-core spatial FFT (default) */
   FFTBF_PREC_TC_FP16 = 1, /* tensor-core GEMM stages, FP16 operands, FP32 accumulate */
-  FFTBF_PREC_TC_BF16 = 2  /* tensor-core GEMM stages, BF16 operands, FP32 accumulate */
+  FFTBF_PREC_TC_BF16 = 2, /* tensor-core GEMM stages, BF16 operands, FP32 accumulate */
+  FFTBF_PREC_TC_FP16X3 = 3 /* tensor-core GEMM stages on split FP16 operands (hi + lo,
+                              three products per stage), FP32 accumulate: FP32 accuracy */
 };
 
 /*
@@ -82,7 +84,10 @@ fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, in
  * as two GEMM stages on 16-bit operands with FP32 accumulation; they need pad_x = 4,
  * pad_y = 512 and at most 256 N-S feeds (FFTBF_EUNSUPPORTED otherwise). With FP16
  * operands the plan scales the E-W output so every intermediate stays finite and
- * removes the scale from the result. Call before fftbf_execute; not thread-safe with it.
+ * removes the scale from the result. FFTBF_PREC_TC_FP16X3 splits every operand into an
+ * FP16 value and its FP16 residual (hi + lo) and forms each stage as hi*hi + hi*lo +
+ * lo*hi in FP32, so the result has FP32 accuracy (the dropped lo*lo term is ~2^-22 of
+ * each product). Call before fftbf_execute; not thread-safe with it.
  */
 int fftbf_plan_set_precision(fftbf_plan* plan, int precision);
 

@@ -18,7 +18,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16",
+__all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16", "PREC_TC_FP16X3",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window", "stacked_shape",
            "stacked_visibilities", "localise",
            "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "Batch", "batch_create",
@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
 
 FFTBF_OK = 0
-PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
+PREC_FP32, PREC_TC_FP16, PREC_TC_BF16, PREC_TC_FP16X3 = 0, 1, 2, 3
 _STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPORTED"}
 
 _lock = threading.Lock()

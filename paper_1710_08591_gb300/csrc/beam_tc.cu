@@ -121,16 +121,18 @@ __device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned 
 struct TcSmem {
   int a1, a2, b1, b2, tw, w, raw, bars, taddr, total;
 };
-__host__ __device__ inline TcSmem tc_smem_layout(int nant) {
+// split: hi and lo halves of every operand (A1 lo at a1 + A1_BYTES, A2 lo of snapshot s
+// at a2 + (2 + s) A2_BYTES, B lo right after B hi).
+__host__ __device__ inline TcSmem tc_smem_layout(int nant, bool split = false) {
   TcSmem L;
   int o = 0;
   auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
   // A1 overlays the first bytes of A2: A1 is consumed by stage 1 before A2 is written,
   // and A2 by stage 2 before the next A1 is written
-  L.a2 = take(2 * tcl::A2_BYTES);
+  L.a2 = take((split ? 4 : 2) * tcl::A2_BYTES);
   L.a1 = L.a2;
-  L.b1 = take(tcl::B1_BYTES);
-  L.b2 = take(tcl::B2_BYTES);
+  L.b1 = take((split ? 2 : 1) * tcl::B1_BYTES);
+  L.b2 = take((split ? 2 : 1) * tcl::B2_BYTES);
   L.tw = take(16 * 32 * 8);
   L.w = take(nant * 8);
   L.raw = take(2 * ((2 * nant + 15) & ~15));
@@ -150,13 +152,15 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
   }
 }
 
-template <bool BF16>
+// SPLIT (FP16 only): every operand is an FP16 value and its FP16 residual, and each stage
+// is hi*hi + hi*lo + lo*hi accumulated in FP32, which gives the result FP32 accuracy.
+template <bool BF16, bool SPLIT = false>
 __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
   const int nant = a.nx * a.ny;
-  const TcSmem L = tc_smem_layout(nant);
+  const TcSmem L = tc_smem_layout(nant, SPLIT);
   unsigned char* a1 = smem + L.a1;
   unsigned char* a2 = smem + L.a2;
   unsigned char* b1s = smem + L.b1;
@@ -187,10 +191,14 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
   }
   load_kmajor(b1s, ta.b1, 64, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
   load_kmajor(b2s, ta.b2, 32, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
+  if constexpr (SPLIT) {
+    load_kmajor(b1s + tcl::B1_BYTES, ta.b1lo, 64, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
+    load_kmajor(b2s + tcl::B2_BYTES, ta.b2lo, 32, tcl::B_LBO, tcl::B_SBO, tid, tcl::NT);
+  }
   // FP16 form: packed-half input stage when the E-W axis is a plain 4-point DFT over
   // groups of four N-S feeds (4-byte words), and packed-half twiddles between the stages.
-  const bool fast16 = !BF16 && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny;
-  if constexpr (!BF16) {
+  const bool fast16 = !BF16 && !SPLIT && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny;
+  if constexpr (!BF16 && !SPLIT) {
     uint2* tw16 = reinterpret_cast<uint2*>(twsm);      // [k1][n2] {(c, d), (-d, c)}
     for (int i = tid; i < 512; i += tcl::NT) {
       const float2 t = a.tw[(i >> 4) * (i & 15)];
@@ -297,8 +305,16 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
 #pragma unroll
       for (int A = 0; A < 4; ++A) {
         const int m = (s * 4 + A) * 16 + (iy & 15);
-        *reinterpret_cast<uint32_t*>(a1 + tc::kmajor_off(m, 2 * (iy >> 4), tcl::A1_LBO, tcl::A1_SBO)) =
-            pack2<BF16>(z[A].x * ta.scale, z[A].y * ta.scale);
+        const uint32_t off = tc::kmajor_off(m, 2 * (iy >> 4), tcl::A1_LBO, tcl::A1_SBO);
+        if constexpr (SPLIT) {
+          const float zr = z[A].x * ta.scale, zi = z[A].y * ta.scale;
+          const __half2 h = __floats2half2_rn(zr, zi);
+          const float2 hf = __half22float2(h);
+          *reinterpret_cast<uint32_t*>(a1 + off) = h2u(h);
+          *reinterpret_cast<uint32_t*>(a1 + tcl::A1_BYTES + off) = pack2<false>(zr - hf.x, zi - hf.y);
+        } else {
+          *reinterpret_cast<uint32_t*>(a1 + off) = pack2<BF16>(z[A].x * ta.scale, z[A].y * ta.scale);
+        }
       }
     }
     tc::fence_proxy_async_smem();
@@ -311,6 +327,19 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
       for (int kk = 0; kk < 2; ++kk)
         tc::mma_f16(tbase, tc::smem_desc(sa + kk * 2 * tcl::A1_LBO, tcl::A1_LBO, tcl::A1_SBO),
                     tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id1, kk);
+      if constexpr (SPLIT) {
+        // + hi * B_lo + lo * B_hi
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tbase, tc::smem_desc(sa + kk * 2 * tcl::A1_LBO, tcl::A1_LBO, tcl::A1_SBO),
+                      tc::smem_desc(sb + tcl::B1_BYTES + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO),
+                      id1, 1);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tbase,
+                      tc::smem_desc(sa + tcl::A1_BYTES + kk * 2 * tcl::A1_LBO, tcl::A1_LBO, tcl::A1_SBO),
+                      tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id1, 1);
+      }
       tc::mma_commit(bar1);
     }
     ok = tc::mbar_wait(bar1, phase, tcl::WAIT_NS);
@@ -331,7 +360,16 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
         for (int j = 0; j < 8; ++j) {
           const int k1 = 8 * q + j;
           uint32_t yv;
-          if constexpr (!BF16) {
+          if constexpr (SPLIT) {
+            const float2 x = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+            const float2 y = cmul(x, twsm[k1 * 16 + n2]);
+            const __half2 h = __floats2half2_rn(y.x, y.y);
+            const float2 hf = __half22float2(h);
+            yv = h2u(h);
+            *reinterpret_cast<uint32_t*>(a2 + (2 + s) * tcl::A2_BYTES +
+                                         tc::kmajor_off(A * 32 + k1, 2 * n2, tcl::A2_LBO, tcl::A2_SBO)) =
+                pack2<false>(y.x - hf.x, y.y - hf.y);
+          } else if constexpr (!BF16) {
             const uint2 t = reinterpret_cast<const uint2*>(twsm)[k1 * 16 + n2];
             const __half2 h = __floats2half2_rn(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
             yv = h2u(__hfma2(__high2half2(h), u2h(t.y), __hmul2(__low2half2(h), u2h(t.x))));
@@ -358,6 +396,20 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
           tc::mma_f16(tbase + 32 * s,
                       tc::smem_desc(sa + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
                       tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id2, kk);
+        if constexpr (SPLIT) {
+          const uint32_t sl = tc::smem_u32(a2 + (2 + s) * tcl::A2_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tbase + 32 * s,
+                        tc::smem_desc(sa + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
+                        tc::smem_desc(sb + tcl::B2_BYTES + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO),
+                        id2, 1);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tbase + 32 * s,
+                        tc::smem_desc(sl + kk * 2 * tcl::A2_LBO, tcl::A2_LBO, tcl::A2_SBO),
+                        tc::smem_desc(sb + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO), id2, 1);
+        }
       }
       tc::mma_commit(bar2);
     }
@@ -773,14 +825,15 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   // The serial kernel (four CTAs per SM, every warp in every phase) measures faster than
   // the warp-specialised pipeline on the 4x256 lattice; FFTBF_TC_PIPE=1 selects the latter.
   const char* pipe = getenv("FFTBF_TC_PIPE");
-  if (!(pipe && pipe[0] && pipe[0] != '0')) {
-    const TcSmem L = tc_smem_layout(a.nx * a.ny);
+  if (ta.split || !(pipe && pipe[0] && pipe[0] != '0')) {   // the split form is serial only
+    const TcSmem L = tc_smem_layout(a.nx * a.ny, ta.split != 0);
     // at most 8 CTAs of 64 TMEM columns per SM: keep a ninth from fitting (registers and
-    // this shared memory hold it at 5 on the 4x256 lattice)
+    // this shared memory hold it at 5 on the 4x256 lattice, 3 for the split form)
     size_t smem = (size_t)L.total;
     if (smem < 26 * 1024) smem = 26 * 1024;
     if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
-    auto kern = ta.bf16 ? beams_tc_kernel<true> : beams_tc_kernel<false>;
+    auto kern = ta.split ? beams_tc_kernel<false, true>
+                         : (ta.bf16 ? beams_tc_kernel<true, false> : beams_tc_kernel<false, false>);
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         cudaSharedmemCarveoutMaxShared));
@@ -814,7 +867,8 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
 // Real-embedded DFT matrices, transposed (row = output, column = input), interleaved
 // (re, im): B1t[2k1 + co][2n1 + ci] from W32^(n1 k1) for n1 < 16, k1 < 32 (the pruned
 // stage 1), B2t[2k2 + co][2n2 + ci] from W16^(n2 k2). FP64, rounded once to 16 bits.
-__global__ void tc_tables_kernel(uint16_t* b1, uint16_t* b2, int bf16) {
+// lo != 0: the FP16 residual v - fp16(v) instead (the low half of a split FP16 operand).
+__global__ void tc_tables_kernel(uint16_t* b1, uint16_t* b2, int bf16, int lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   auto entry = [](int out_c, int in_c, double c, double sp) {
     // X_re = x_re C - x_im S', X_im = x_re S' + x_im C with W = C + i S'
@@ -824,6 +878,10 @@ __global__ void tc_tables_kernel(uint16_t* b1, uint16_t* b2, int bf16) {
   auto store = [&](uint16_t* dst, double v) {
     if (bf16) {
       __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      *dst = *reinterpret_cast<uint16_t*>(&h);
+    } else if (lo) {
+      const __half hi = __float2half_rn((float)v);
+      __half h = __float2half_rn((float)(v - (double)__half2float(hi)));
       *dst = *reinterpret_cast<uint16_t*>(&h);
     } else {
       __half h = __float2half_rn((float)v);
@@ -847,7 +905,13 @@ __global__ void tc_tables_kernel(uint16_t* b1, uint16_t* b2, int bf16) {
 }
 
 int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st) {
-  tc_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, bf16 ? 1 : 0);
+  tc_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, bf16 ? 1 : 0, 0);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st) {
+  tc_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, 0, 1);
   FFTBF_CUDA_TRY(cudaGetLastError());
   return FFTBF_OK;
 }

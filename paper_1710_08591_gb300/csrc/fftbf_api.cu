@@ -122,7 +122,7 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
     p->precision = prec;
     return FFTBF_OK;
   }
-  if (prec != FFTBF_PREC_TC_FP16 && prec != FFTBF_PREC_TC_BF16)
+  if (prec != FFTBF_PREC_TC_FP16 && prec != FFTBF_PREC_TC_BF16 && prec != FFTBF_PREC_TC_FP16X3)
     return set_error(FFTBF_EINVAL, "unknown precision %d", prec);
   if (!tc_supported(p->nx, p->ny, p->mx, p->my))
     return set_error(FFTBF_EUNSUPPORTED,
@@ -136,6 +136,14 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
   const bool bf16 = prec == FFTBF_PREC_TC_BF16;
   int rc = build_tc_tables(p->d_b1, p->d_b2, bf16, 0);
   if (rc != FFTBF_OK) return rc;
+  if (prec == FFTBF_PREC_TC_FP16X3) {
+    if (!p->d_b1lo) {
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_b1lo, sizeof(uint16_t) * 64 * 32));
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_b2lo, sizeof(uint16_t) * 32 * 32));
+    }
+    rc = build_tc_tables_lo(p->d_b1lo, p->d_b2lo, 0);
+    if (rc != FFTBF_OK) return rc;
+  }
   FFTBF_CUDA_TRY(cudaDeviceSynchronize());
   // FP16 range: |X1| <= 16 * max_iy sum_ix |w| * 8 sqrt(2); keep it below 30000.
   double wmax = 0.0;
@@ -191,6 +199,9 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
     ta.scale = p->tc_scale;
     ta.err = p->d_err;
     ta.bf16 = p->precision == FFTBF_PREC_TC_BF16;
+    ta.split = p->precision == FFTBF_PREC_TC_FP16X3;
+    ta.b1lo = p->d_b1lo;
+    ta.b2lo = p->d_b2lo;
     rc = launch_beams_tc(ta, p->nsm, st);
   }
   if (rc == FFTBF_OK) remember_stream(p, st);
@@ -278,6 +289,8 @@ void fftbf_destroy(fftbf_plan* p) {
     cudaFree(p->d_tw);
     cudaFree(p->d_b1);
     cudaFree(p->d_b2);
+    cudaFree(p->d_b1lo);
+    cudaFree(p->d_b2lo);
     cudaFree(p->d_err);
   }
   delete p;

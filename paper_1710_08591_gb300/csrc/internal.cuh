@@ -84,10 +84,14 @@ struct TcArgs {
   float scale;          // multiplies the E-W output before rounding to 16 bits
   int* err;             // device error word (FFTBF_ETIMEOUT on a wait that ran out)
   int bf16;
+  int split;            // split FP16: b1lo, b2lo hold the residuals of b1, b2
+  const uint16_t* b1lo;
+  const uint16_t* b2lo;
 };
 bool tc_supported(int nx, int ny, int mx, int my);
 int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st);
 int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st);
+int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st);
 int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
                          float* D, int* err, cudaStream_t st);
 int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st);
@@ -166,6 +170,8 @@ struct fftbf_plan {
   std::vector<float> h_w;         // host copy of the weights (re, im interleaved)
   uint16_t* d_b1 = nullptr;       // tensor-core stage matrices for the selected precision
   uint16_t* d_b2 = nullptr;
+  uint16_t* d_b1lo = nullptr;     // split FP16 form: residuals of the stage matrices
+  uint16_t* d_b2lo = nullptr;
   float tc_scale = 1.f;
   int* d_err = nullptr;           // device error word of bounded waits
   std::vector<cudaStream_t> streams_used;

@@ -15,6 +15,11 @@ import paper_1710_08591_gb300 as fb  # noqa: E402
 # 11-bit (FP16) or 8-bit (BF16) significands, before each GEMM stage).
 TOL_TC = {"fp16": 5e-3, "bf16": 3e-2}
 RMS_TC = {"fp16": 1e-3, "bf16": 6e-3}
+# The split-FP16 form (hi + lo operands, three products per stage) is held to the FP32
+# form's bound: 1e-5 of each beam.
+TOL_TC["fp16x3"] = 1e-5
+RMS_TC["fp16x3"] = 2e-6
+PREC = {"fp16": fb.PREC_TC_FP16, "bf16": fb.PREC_TC_BF16, "fp16x3": fb.PREC_TC_FP16X3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,7 +56,7 @@ def run_tc(v, w, shape, form):
     dv = torch.from_numpy(np.ascontiguousarray(v).reshape(-1)).cuda()
     out = torch.full((T // n_int, nfreq, mx, my), float("nan"), device="cuda")
     with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
-        fb.plan_set_precision(plan, fb.PREC_TC_FP16 if form == "fp16" else fb.PREC_TC_BF16)
+        fb.plan_set_precision(plan, PREC[form])
         fb.execute(plan, dv, T, out)
         fb.plan_sync(plan)
     return out.cpu().numpy()
@@ -64,7 +69,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("form", ["fp16", "bf16", "fp16x3"])
 @pytest.mark.parametrize("shape,wk", SHAPES, ids=lambda x: "x".join(map(str, x)) if isinstance(x, tuple) else x)
 def test_tc_beams_match_oracle(form, shape, wk):
     v, w = make_case(*shape, weights=wk, seed=31)
