@@ -87,9 +87,13 @@ __device__ __forceinline__ void dft4_h2(__half2* v) {
 // so each E-W beam A is one 16-byte core-matrix row (one store), lanes run over n2 (the
 // stores of a warp fill all banks) and the weights [ix][iy] are read 128 bytes at a time.
 // Feeds iy >= ny and a missing second snapshot (odd n_int * npol) give zeros.
+// REALW: real weights, one half2 (scale w / 16, scale w) per feed and one HMUL2.
+template <bool REALW = false>
 __device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned char* raw,
-                                              const uint2* w16, int nant, int ny, int tid,
+                                              const void* wtab, int nant, int ny, int tid,
                                               bool snap1_ok, int lbo, int sbo) {
+  const uint2* w16 = reinterpret_cast<const uint2*>(wtab);
+  const uint32_t* w16r = reinterpret_cast<const uint32_t*>(wtab);
   const int s = tid >> 6, j = (tid >> 4) & 3, n2 = tid & 15;
   const bool sok = s == 0 || snap1_ok;
   const unsigned char* rs = raw + s * nant;
@@ -104,8 +108,14 @@ __device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned 
 #pragma unroll
       for (int ix = 0; ix < 4; ++ix) {
         const __half2 x = unpack16((uint32_t)rs[ix * ny + iy], 0);
-        const uint2 wv = w16[ix * ny + iy];
-        z[ix] = __hfma2(__high2half2(x), u2h(wv.y), __hmul2(__low2half2(x), u2h(wv.x)));
+        if constexpr (REALW) {
+          // _rn: the product is rounded before the E-W adds (no fusing into them), as in
+          // the complex-weight path, so both paths give bit-identical results
+          z[ix] = __hmul2_rn(x, u2h(w16r[ix * ny + iy]));
+        } else {
+          const uint2 wv = w16[ix * ny + iy];
+          z[ix] = __hfma2(__high2half2(x), u2h(wv.y), __hmul2(__low2half2(x), u2h(wv.x)));
+        }
       }
       dft4_h2(z);
     }
@@ -123,7 +133,7 @@ struct TcSmem {
 };
 // split: hi and lo halves of every operand (A1 lo at a1 + A1_BYTES, A2 lo of snapshot s
 // at a2 + (2 + s) A2_BYTES, B lo right after B hi).
-__host__ __device__ inline TcSmem tc_smem_layout(int nant, bool split = false) {
+__host__ __device__ inline TcSmem tc_smem_layout(int nant, bool split = false, bool w4 = false) {
   TcSmem L;
   int o = 0;
   auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
@@ -134,7 +144,7 @@ __host__ __device__ inline TcSmem tc_smem_layout(int nant, bool split = false) {
   L.b1 = take((split ? 2 : 1) * tcl::B1_BYTES);
   L.b2 = take((split ? 2 : 1) * tcl::B2_BYTES);
   L.tw = take(16 * 32 * 8);
-  L.w = take(nant * 8);
+  L.w = take(nant * (w4 ? 4 : 8));            // 4 bytes per feed: real FP16-form weights
   L.raw = take(2 * ((2 * nant + 15) & ~15));
   L.bars = take(16);
   L.taddr = take(16);
@@ -155,12 +165,12 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 // SPLIT (FP16 only): every operand is an FP16 value and its FP16 residual, and each stage
 // is hi*hi + hi*lo + lo*hi accumulated in FP32, which gives the result FP32 accuracy.
 template <bool BF16, bool SPLIT = false>
-__global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
+__global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
   const int nant = a.nx * a.ny;
-  const TcSmem L = tc_smem_layout(nant, SPLIT);
+  const TcSmem L = tc_smem_layout(nant, SPLIT, ta.w4 != 0);
   unsigned char* a1 = smem + L.a1;
   unsigned char* a2 = smem + L.a2;
   unsigned char* b1s = smem + L.b1;
@@ -207,7 +217,15 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
   } else {
     for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
   }
-  if (fast16) {
+  if (fast16 && ta.w4) {
+    // real weights: per feed (scale w / 16, scale w), (16 re, im) -> scale (re + i im) w
+    uint32_t* w16r = reinterpret_cast<uint32_t*>(wsm);
+    const float sc = ta.scale;
+    for (int i = tid; i < nant; i += tcl::NT) {
+      const float w = a.w[i].x;
+      w16r[i] = pack2<false>(w * sc * 0.0625f, w * sc);
+    }
+  } else if (fast16) {
     // per feed {scale w / 16, scale i w}: (16 re, im) -> scale (re + i im) w
     uint2* w16 = reinterpret_cast<uint2*>(wsm);
     const float sc = ta.scale;
@@ -279,8 +297,12 @@ __global__ void __launch_bounds__(tcl::NT, 5) beams_tc_kernel(const TcArgs ta) {
     // ---- unpack x weight, E-W DFT, scale, round: stage-1 operand A1[(s,A,n2)][(n1,c)]
     const unsigned char* raw = raw0 + cur * rawsz;
     if (fast16) {
-      input_stage16(a1, raw, reinterpret_cast<const uint2*>(wsm), nant, a.ny, tid,
-                    2 * it + 1 < nsnap, tcl::A1_LBO, tcl::A1_SBO);
+      if (ta.w4)
+        input_stage16<true>(a1, raw, wsm, nant, a.ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
+                            tcl::A1_SBO);
+      else
+        input_stage16<false>(a1, raw, wsm, nant, a.ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
+                             tcl::A1_SBO);
     } else
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -614,7 +636,7 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
       const unsigned char* raw = raw0 + (p & 1) * rawsz;
       unsigned char* a1b = a1 + b * tcl::A1_BYTES;
       if (fast16) {
-        input_stage16(a1b, raw, reinterpret_cast<const uint2*>(wsm), nant, a.ny, tid,
+        input_stage16<false>(a1b, raw, wsm, nant, a.ny, tid,
                       2 * it + 1 < nsnap, tcl::A1_LBO, tcl::A1_SBO);
       } else
 #pragma unroll
@@ -826,7 +848,7 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   // the warp-specialised pipeline on the 4x256 lattice; FFTBF_TC_PIPE=1 selects the latter.
   const char* pipe = getenv("FFTBF_TC_PIPE");
   if (ta.split || !(pipe && pipe[0] && pipe[0] != '0')) {   // the split form is serial only
-    const TcSmem L = tc_smem_layout(a.nx * a.ny, ta.split != 0);
+    const TcSmem L = tc_smem_layout(a.nx * a.ny, ta.split != 0, ta.w4 != 0);
     // at most 8 CTAs of 64 TMEM columns per SM: keep a ninth from fitting (registers and
     // this shared memory hold it at 5 on the 4x256 lattice, 3 for the split form)
     size_t smem = (size_t)L.total;

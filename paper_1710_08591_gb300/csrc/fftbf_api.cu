@@ -100,6 +100,8 @@ fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, in
       p->h_w[2 * i] = weights ? weights[2 * i] : 1.f;
       p->h_w[2 * i + 1] = weights ? weights[2 * i + 1] : 0.f;
     }
+    p->real_w = true;
+    for (int i = 0; i < nant; ++i) p->real_w = p->real_w && p->h_w[2 * i + 1] == 0.f;
     e = cudaMemcpy(p->d_w, p->h_w.data(), sizeof(float2) * nant, cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
@@ -200,6 +202,9 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
     ta.err = p->d_err;
     ta.bf16 = p->precision == FFTBF_PREC_TC_BF16;
     ta.split = p->precision == FFTBF_PREC_TC_FP16X3;
+    // the packed-half input stage with real weights: 4 bytes per feed in shared memory
+    ta.w4 = p->precision == FFTBF_PREC_TC_FP16 && p->real_w && a.ew_dft && p->nx == 4 &&
+            (p->ny & 3) == 0 && a.nyf == p->ny;
     ta.b1lo = p->d_b1lo;
     ta.b2lo = p->d_b2lo;
     rc = launch_beams_tc(ta, p->nsm, st);

@@ -85,6 +85,7 @@ struct TcArgs {
   int* err;             // device error word (FFTBF_ETIMEOUT on a wait that ran out)
   int bf16;
   int split;            // split FP16: b1lo, b2lo hold the residuals of b1, b2
+  int w4;               // FP16 form with real weights on the packed-half input stage
   const uint16_t* b1lo;
   const uint16_t* b2lo;
 };
@@ -168,6 +169,7 @@ struct fftbf_plan {
   fftbf::TiedTables tied;
   fftbf::HostPipe pipe;
   std::vector<float> h_w;         // host copy of the weights (re, im interleaved)
+  bool real_w = false;            // every weight has a zero imaginary part
   uint16_t* d_b1 = nullptr;       // tensor-core stage matrices for the selected precision
   uint16_t* d_b2 = nullptr;
   uint16_t* d_b1lo = nullptr;     // split FP16 form: residuals of the stage matrices

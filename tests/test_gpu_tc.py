@@ -94,7 +94,8 @@ def test_tc_serial_kernel_matches_pipelined(form, monkeypatch):
     serial = run_tc(v, w, shape, form)
     monkeypatch.setenv("FFTBF_TC_PIPE", "1")
     piped = run_tc(v, w, shape, form)
-    assert np.array_equal(piped, serial)
+    diff = np.abs(piped - serial) / np.abs(serial)
+    assert np.array_equal(piped, serial), f"max rel diff {diff.max():.3e} at {np.argmax(diff)}"
 
 
 def test_tc_bit_identical_alone_and_in_batch():
