@@ -121,9 +121,20 @@ beams_fp32_n512_kernel(const BeamArgs a) {
         const uint8_t* rs = raw + s * nant;
         if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
           if (a.ew_dft) {
+            if (a.real_w) {
+              // real weights: w x in two multiplies (the same roundings as the complex
+              // product with a zero imaginary part)
 #pragma unroll
-            for (int ix = 0; ix < MX; ++ix)
-              z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+              for (int ix = 0; ix < MX; ++ix) {
+                const float wr = wsm[ix * a.ny + iy].x;
+                const float2 xv = unpack_byte(rs[ix * a.ny + iy]);
+                z[ix] = make_float2(wr * xv.x, wr * xv.y);
+              }
+            } else {
+#pragma unroll
+              for (int ix = 0; ix < MX; ++ix)
+                z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+            }
             Dft<MX>::run(z);
           }
         }

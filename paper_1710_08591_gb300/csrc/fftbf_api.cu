@@ -184,6 +184,7 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
   a.nyf = std::min(p->ny, p->my);
   a.nwin = T / p->n_int;
   a.ew_dft = (p->mx == p->nx) && (p->mx & (p->mx - 1)) == 0 && p->mx <= 16;
+  a.real_w = p->real_w ? 1 : 0;
   const int nsnap = p->n_int * p->npol;
   int S = kMaxElems / (p->mx * p->my);
   if (S < 1) S = 1;

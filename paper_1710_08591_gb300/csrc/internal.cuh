@@ -51,6 +51,7 @@ struct BeamArgs {
   int nst;                // FFT stages (power-of-two my): r0 first, then radix 8
   int r0;                 // radix of the first stage (1, 2, 4 or 8)
   int ew_dft;             // 1 if mx == nx and mx is a power of two (E-W is a plain DFT)
+  int real_w;             // 1 if every weight is real (two multiplies instead of a complex one)
   int64_t nwin;           // windows in this call
 };
 
