@@ -82,10 +82,11 @@ __device__ __noinline__ void batch_item(const BeamArgs& a, int64_t item, unsigne
   float acc[NACC];
 #pragma unroll
   for (int i = 0; i < NACC; ++i) acc[i] = 0.f;
-  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage_bytes(a, smem, ivol, 0, nsnap, nant, vec16);
   cp_async_commit();
   for (int it = 0; it < niter; ++it) {
-    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, ivol, it + 1, nsnap, nant, vec16);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();

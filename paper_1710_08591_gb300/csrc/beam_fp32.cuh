@@ -266,21 +266,42 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stage the bytes of snapshots it*S .. it*S+S-1 of work item `item` into raw.
-__device__ __forceinline__ void stage_bytes(const BeamArgs& a, uint8_t* raw, int64_t item,
-                                            int it, int nsnap, int nant, bool vec16) {
+// Voltages are [t][f][p][feed]. First byte of work item `item` (window jw = item / nfreq,
+// channel f): snapshot 0 of time jw n_int. One 64-bit division per work item.
+__device__ __forceinline__ const uint8_t* item_volts(const BeamArgs& a, int64_t item, int nant) {
   const int64_t jw = item / a.nfreq;
   const int f = (int)(item - jw * a.nfreq);
+  return a.volts + ((jw * a.n_int * a.nfreq + f) * a.npol) * (int64_t)nant;
+}
+// Offset of snapshot g (time g / npol, pol g % npol) from the first byte of its work item.
+__device__ __forceinline__ int64_t snap_offset(const BeamArgs& a, int g, int nant) {
+  int tt, p;
+  if (a.npol == 2) {
+    tt = g >> 1;
+    p = g & 1;
+  } else if (a.npol == 1) {
+    tt = g;
+    p = 0;
+  } else {
+    tt = g / a.npol;
+    p = g - tt * a.npol;
+  }
+  return ((int64_t)tt * a.nfreq * a.npol + p) * (int64_t)nant;
+}
+
+// Stage the bytes of snapshots it*S .. it*S+S-1 of the work item starting at ivol into raw.
+__device__ __forceinline__ void stage_bytes(const BeamArgs& a, uint8_t* raw, const uint8_t* ivol,
+                                            int it, int nsnap, int nant, bool vec16) {
   if (vec16) {
     const int cps = nant >> 4;              // 16-byte chunks per snapshot
     const int nchunk = a.S * cps;
+    const bool pow2 = (cps & (cps - 1)) == 0;
+    const int lcps = __ffs(cps) - 1;
     for (int q = threadIdx.x; q < nchunk; q += kThreads) {
-      const int s = q / cps;
+      const int s = pow2 ? q >> lcps : q / cps;
       const int g = it * a.S + s;
       if (g < nsnap) {
-        const int64_t t = jw * a.n_int + g / a.npol;
-        const int p = g % a.npol;
-        const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + p) * (int64_t)nant;
+        const uint8_t* src = ivol + snap_offset(a, g, nant);
         cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
       }
     }
@@ -289,11 +310,7 @@ __device__ __forceinline__ void stage_bytes(const BeamArgs& a, uint8_t* raw, int
     for (int q = threadIdx.x; q < nb; q += kThreads) {
       const int s = q / nant;
       const int g = it * a.S + s;
-      if (g < nsnap) {
-        const int64_t t = jw * a.n_int + g / a.npol;
-        const int p = g % a.npol;
-        raw[q] = a.volts[((t * a.nfreq + f) * a.npol + p) * (int64_t)nant + (q - s * nant)];
-      }
+      if (g < nsnap) raw[q] = ivol[snap_offset(a, g, nant) + (q - s * nant)];
     }
   }
 }
@@ -325,7 +342,8 @@ __global__ void __launch_bounds__(kThreads, FFTBF_FP32_MIN_BLOCKS) beams_fp32_ke
   int64_t item = blockIdx.x;
   if (item >= nitems) return;
   int it = 0, cur = 0;
-  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage_bytes(a, smem, ivol, 0, nsnap, nant, vec16);
   cp_async_commit();
 
   constexpr int NACC = kMaxElems / kThreads;
@@ -338,7 +356,8 @@ __global__ void __launch_bounds__(kThreads, FFTBF_FP32_MIN_BLOCKS) beams_fp32_ke
     int nit = it + 1;
     if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
     const bool has_next = nitem < nitems;
-    if (has_next) stage_bytes(a, smem + (cur ^ 1) * rawsz, nitem, nit, nsnap, nant, vec16);
+    const uint8_t* nvol = nit == 0 && has_next ? item_volts(a, nitem, nant) : ivol;
+    if (has_next) stage_bytes(a, smem + (cur ^ 1) * rawsz, nvol, nit, nsnap, nant, vec16);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -419,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, FFTBF_FP32_MIN_BLOCKS) beams_fp32_ke
     }
     if (!has_next) break;
     item = nitem;
+    ivol = nvol;
     it = nit;
     cur ^= 1;
   }

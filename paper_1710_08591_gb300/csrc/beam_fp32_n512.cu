@@ -31,14 +31,18 @@ constexpr int kRegion = 32 * 17;   // float2 slots per transform region (X1 tile
 #define FFTBF_N512_MIN_BLOCKS (24 / FFTBF_N512_NW)   // CTAs per SM the register budget targets
 #endif
 
-template <int MX>
+// NY256: 256 N-S feeds in every row, all of them live, E-W axis a plain MX-point DFT and
+// 16-byte aligned voltages (the feed offsets of the input stage become constants).
+template <int MX, bool NY256 = false>
 __global__ void __launch_bounds__((MX > 4 ? MX : FFTBF_N512_NW) * 32, MX > 4 ? 2 : FFTBF_N512_MIN_BLOCKS)
 beams_fp32_n512_kernel(const BeamArgs a) {
   constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;   // warps per CTA = transforms per iteration
   constexpr int S = NW / MX;                // snapshots per iteration
   constexpr int NT = NW * 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nant = a.nx * a.ny;
+  const int ny = NY256 ? 256 : a.ny;
+  const int nyf = NY256 ? 256 : a.nyf;
+  const int nant = NY256 ? MX * 256 : a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
   float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
   float2* exsm = wsm + nant;
@@ -50,7 +54,8 @@ beams_fp32_n512_kernel(const BeamArgs a) {
   const int nsnap = a.n_int * a.npol;
   const int niter = (nsnap + S - 1) / S;
   const int64_t nitems = a.nwin * a.nfreq;
-  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const bool vec16 =
+      NY256 || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
 
   for (int i = threadIdx.x; i < nant; i += NT) wsm[i] = a.w[i];
   for (int i = threadIdx.x; i < MX * a.nx; i += NT) exsm[i] = a.ex[i];
@@ -63,35 +68,28 @@ beams_fp32_n512_kernel(const BeamArgs a) {
   int64_t item = blockIdx.x;
   if (item >= nitems) return;
 
-  // byte staging for (item, it) into buffer b
-  auto stage = [&](int64_t itm, int it, int b) {
+  // byte staging of iteration `it` of the work item starting at ivol into buffer b
+  auto stage = [&](const uint8_t* ivol, int it, int b) {
     uint8_t* raw = smem + b * rawsz;
-    const int64_t jw = itm / a.nfreq;
-    const int f = (int)(itm - jw * a.nfreq);
     if (vec16) {
       const int cps = nant >> 4;
       for (int q = threadIdx.x; q < S * cps; q += NT) {
         const int s = q / cps, g = it * S + s;
         if (g < nsnap) {
-          const int64_t t = jw * a.n_int + g / a.npol;
-          const int p = g % a.npol;
-          const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + p) * (int64_t)nant;
+          const uint8_t* src = ivol + snap_offset(a, g, nant);
           cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
         }
       }
     } else {
       for (int q = threadIdx.x; q < S * nant; q += NT) {
         const int s = q / nant, g = it * S + s;
-        if (g < nsnap) {
-          const int64_t t = jw * a.n_int + g / a.npol;
-          const int p = g % a.npol;
-          raw[q] = a.volts[((t * a.nfreq + f) * a.npol + p) * (int64_t)nant + (q - s * nant)];
-        }
+        if (g < nsnap) raw[q] = ivol[snap_offset(a, g, nant) + (q - s * nant)];
       }
     }
   };
 
-  stage(item, 0, 0);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage(ivol, 0, 0);
   cp_async_commit();
   float acc[16];
 #pragma unroll
@@ -105,42 +103,44 @@ beams_fp32_n512_kernel(const BeamArgs a) {
     int nit = it + 1;
     if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
     const bool has_next = nitem < nitems;
+    const uint8_t* nvol = nit == 0 && has_next ? item_volts(a, nitem, nant) : ivol;
     cp_async_wait<0>();
     __syncthreads();                                  // (A) bytes of `it` visible; regions free
-    if (has_next) stage(nitem, nit, cur ^ 1);
+    if (has_next) stage(nvol, nit, cur ^ 1);
     cp_async_commit();
 
     // ---- unpack x weight, E-W transform -> Z[s*MX + A][pad16(iy)]
     const uint8_t* raw = smem + cur * rawsz;
-    for (int c = threadIdx.x; c < S * 256; c += NT) {
+#pragma unroll(NY256 ? S * 256 / NT : 1)
+    for (int r = 0, c = threadIdx.x; NY256 ? r < S * 256 / NT : c < S * 256; ++r, c += NT) {
       const int s = c >> 8, iy = c & 255;
       float2 z[MX];
 #pragma unroll
       for (int A = 0; A < MX; ++A) z[A] = czero();
-      if (iy < a.nyf && it * S + s < nsnap) {
+      if (iy < nyf && it * S + s < nsnap) {
         const uint8_t* rs = raw + s * nant;
         if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
-          if (a.ew_dft) {
+          if (NY256 || a.ew_dft) {
             if (a.real_w) {
               // real weights: w x in two multiplies (the same roundings as the complex
               // product with a zero imaginary part)
 #pragma unroll
               for (int ix = 0; ix < MX; ++ix) {
-                const float wr = wsm[ix * a.ny + iy].x;
-                const float2 xv = unpack_byte(rs[ix * a.ny + iy]);
+                const float wr = wsm[ix * ny + iy].x;
+                const float2 xv = unpack_byte(rs[ix * ny + iy]);
                 z[ix] = make_float2(wr * xv.x, wr * xv.y);
               }
             } else {
 #pragma unroll
               for (int ix = 0; ix < MX; ++ix)
-                z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+                z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
             }
             Dft<MX>::run(z);
           }
         }
-        if (!a.ew_dft) {
+        if (!NY256 && !a.ew_dft) {
           for (int ix = 0; ix < a.nx; ++ix) {
-            const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+            const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
 #pragma unroll
             for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
           }
@@ -199,6 +199,7 @@ beams_fp32_n512_kernel(const BeamArgs a) {
     }
     if (!has_next) break;
     item = nitem;
+    ivol = nvol;
     it = nit;
     cur ^= 1;
   }
@@ -217,7 +218,9 @@ static int launch_n512_mx(const BeamArgs& a, int nsm, cudaStream_t st) {
   constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;
   constexpr int S = NW / MX;
   const size_t smem = n512_smem_bytes(a, S, NW);
-  auto kern = beams_fp32_n512_kernel<MX>;
+  const bool ny256 = MX == 4 && a.ew_dft && a.nx == MX && a.ny == 256 && a.nyf == 256 &&
+                     (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
+  auto kern = ny256 ? beams_fp32_n512_kernel<MX, MX == 4> : beams_fp32_n512_kernel<MX>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));

@@ -160,10 +160,11 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
 #pragma unroll
     for (int k = 0; k < R; ++k) acc[j][k] = 0.f;
 
-  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage_bytes(a, smem, ivol, 0, nsnap, nant, vec16);
   cp_async_commit();
   for (int it = 0; it < niter; ++it) {
-    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, ivol, it + 1, nsnap, nant, vec16);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();                                  // bytes of `it` visible; regions free
@@ -292,10 +293,11 @@ __device__ __forceinline__ void warp2_item(const BeamArgs& a, int64_t item, unsi
   float acc[32];
 #pragma unroll
   for (int k = 0; k < 32; ++k) acc[k] = 0.f;
-  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage_bytes(a, smem, ivol, 0, nsnap, nant, vec16);
   cp_async_commit();
   for (int it = 0; it < niter; ++it) {
-    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, ivol, it + 1, nsnap, nant, vec16);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -382,10 +384,11 @@ __device__ __forceinline__ void lane_item16(const BeamArgs& a, int64_t item, uns
   float acc[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) acc[k] = 0.f;
-  stage_bytes(a, smem, item, 0, nsnap, nant, vec16);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage_bytes(a, smem, ivol, 0, nsnap, nant, vec16);
   cp_async_commit();
   for (int it = 0; it < niter; ++it) {
-    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, item, it + 1, nsnap, nant, vec16);
+    if (it + 1 < niter) stage_bytes(a, smem + ((it + 1) & 1) * rawsz, ivol, it + 1, nsnap, nant, vec16);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();

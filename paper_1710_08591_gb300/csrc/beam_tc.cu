@@ -82,6 +82,14 @@ __device__ __forceinline__ void dft4_h2(__half2* v) {
   v[3] = __hfma2(dsw, u2h(0x3C00BC00u), b);            // b + i d: (-1, 1)
 }
 
+// Slot of N-S feed iy within its row of the 4-byte weight table: bit 6 of iy is XORed
+// into bit 4 when rows hold a multiple of 32 feeds (a permutation of each aligned block of
+// 128), so that feeds 64 apart, read by the two half-warps of the input stage at the same
+// time, sit 16 banks apart.
+__device__ __forceinline__ int w4_pos(int iy, int ny) {
+  return (ny & 31) == 0 ? iy ^ ((iy & 64) >> 2) : iy;
+}
+
 // FP16 form, stage-1 operand of one snapshot pair: A1[(s, A, n2)][(n1, c)] = scale x the
 // E-W DFT of w x over the feeds iy = n2 + 16 n1. Thread (s, j, n2) forms n1 = 4j .. 4j + 3,
 // so each E-W beam A is one 16-byte core-matrix row (one store), lanes run over n2 (the
@@ -97,6 +105,8 @@ __device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned 
   const int s = tid >> 6, j = (tid >> 4) & 3, n2 = tid & 15;
   const bool sok = s == 0 || snap1_ok;
   const unsigned char* rs = raw + s * nant;
+  // w4_pos(iy) = iy ^ wsw: bit 6 of iy = n2 + 64 j + 16 kk is the low bit of j
+  const int wsw = (ny & 31) == 0 ? (j & 1) << 4 : 0;
   uint32_t o[4][4];
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
@@ -111,7 +121,7 @@ __device__ __forceinline__ void input_stage16(unsigned char* a1, const unsigned 
         if constexpr (REALW) {
           // _rn: the product is rounded before the E-W adds (no fusing into them), as in
           // the complex-weight path, so both paths give bit-identical results
-          z[ix] = __hmul2_rn(x, u2h(w16r[ix * ny + iy]));
+          z[ix] = __hmul2_rn(x, u2h(w16r[ix * ny + (iy ^ wsw)]));
         } else {
           const uint2 wv = w16[ix * ny + iy];
           z[ix] = __hfma2(__high2half2(x), u2h(wv.y), __hmul2(__low2half2(x), u2h(wv.x)));
@@ -223,7 +233,8 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
     const float sc = ta.scale;
     for (int i = tid; i < nant; i += tcl::NT) {
       const float w = a.w[i].x;
-      w16r[i] = pack2<false>(w * sc * 0.0625f, w * sc);
+      const int ix = i / a.ny, iy = i - ix * a.ny;
+      w16r[ix * a.ny + w4_pos(iy, a.ny)] = pack2<false>(w * sc * 0.0625f, w * sc);
     }
   } else if (fast16) {
     // per feed {scale w / 16, scale i w}: (16 re, im) -> scale (re + i im) w
@@ -248,28 +259,21 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   const uint32_t id2 = tc::idesc_f16(128, 32, BF16);
   const float inv_s2 = 1.0f / (ta.scale * ta.scale);
 
-  auto stage = [&](int64_t itm, int it, unsigned char* raw) {
-    const int64_t jw = itm / a.nfreq;
-    const int f = (int)(itm - jw * a.nfreq);
+  // bytes of snapshot pair `it` of the work item starting at ivol
+  auto stage = [&](const uint8_t* ivol, int it, unsigned char* raw) {
     if (vec16) {
       const int cps = nant >> 4;
       for (int q = tid; q < 2 * cps; q += tcl::NT) {
-        const int s = q / cps, g = 2 * it + s;
+        const int s = q >= cps ? 1 : 0, g = 2 * it + s;      // q < 2 cps
         if (g < nsnap) {
-          const int64_t t = jw * a.n_int + g / a.npol;
-          const int p = g % a.npol;
-          const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + p) * (int64_t)nant;
+          const uint8_t* src = ivol + snap_offset(a, g, nant);
           cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
         }
       }
     } else {
       for (int q = tid; q < 2 * nant; q += tcl::NT) {
         const int s = q / nant, g = 2 * it + s;
-        if (g < nsnap) {
-          const int64_t t = jw * a.n_int + g / a.npol;
-          const int p = g % a.npol;
-          raw[q] = a.volts[((t * a.nfreq + f) * a.npol + p) * (int64_t)nant + (q - s * nant)];
-        }
+        if (g < nsnap) raw[q] = ivol[snap_offset(a, g, nant) + (q - s * nant)];
       }
     }
   };
@@ -281,7 +285,8 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   float acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-  stage(item, 0, raw0);
+  const uint8_t* ivol = item_volts(a, item, nant);
+  stage(ivol, 0, raw0);
   cp_async_commit();
 
   while (true) {
@@ -289,9 +294,10 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
     int nit = it + 1;
     if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
     const bool has_next = nitem < nitems;
+    const uint8_t* nvol = nit == 0 && has_next ? item_volts(a, nitem, nant) : ivol;
     cp_async_wait<0>();
     __syncthreads();                                            // (S1)
-    if (has_next) stage(nitem, nit, raw0 + (cur ^ 1) * rawsz);
+    if (has_next) stage(nvol, nit, raw0 + (cur ^ 1) * rawsz);
     cp_async_commit();
 
     // ---- unpack x weight, E-W DFT, scale, round: stage-1 operand A1[(s,A,n2)][(n1,c)]
@@ -468,6 +474,7 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
     }
     if (!has_next) break;
     item = nitem;
+    ivol = nvol;
     it = nit;
     cur ^= 1;
   }
@@ -591,41 +598,35 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
     // ================================================================ producers
     const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
     const bool scaled = ta.scale != 1.f;
-    auto stage = [&](int64_t itm, int it, unsigned char* raw) {
-      const int64_t jw = itm / a.nfreq;
-      const int f = (int)(itm - jw * a.nfreq);
+    auto stage = [&](const uint8_t* ivol, int it, unsigned char* raw) {
       if (vec16) {
         const int cps = nant >> 4;
         for (int q = tid; q < 2 * cps; q += 128) {
-          const int s = q / cps, g = 2 * it + s;
+          const int s = q >= cps ? 1 : 0, g = 2 * it + s;      // q < 2 cps
           if (g < nsnap) {
-            const int64_t t = jw * a.n_int + g / a.npol;
-            const int pp = g % a.npol;
-            const uint8_t* src = a.volts + ((t * a.nfreq + f) * a.npol + pp) * (int64_t)nant;
+            const uint8_t* src = ivol + snap_offset(a, g, nant);
             cp_async16(raw + s * nant + ((q - s * cps) << 4), src + ((q - s * cps) << 4));
           }
         }
       } else {
         for (int q = tid; q < 2 * nant; q += 128) {
           const int s = q / nant, g = 2 * it + s;
-          if (g < nsnap) {
-            const int64_t t = jw * a.n_int + g / a.npol;
-            const int pp = g % a.npol;
-            raw[q] = a.volts[((t * a.nfreq + f) * a.npol + pp) * (int64_t)nant + (q - s * nant)];
-          }
+          if (g < nsnap) raw[q] = ivol[snap_offset(a, g, nant) + (q - s * nant)];
         }
       }
     };
     int64_t item = blockIdx.x;
     int it = 0;
-    stage(item, 0, raw0);
+    const uint8_t* ivol = item_volts(a, item, nant);
+    stage(ivol, 0, raw0);
     cp_async_commit();
     for (int64_t p = 0; p < P; ++p) {
       int64_t nitem = item;
       int nit = it + 1;
       if (nit == niter) { nitem = item + gridDim.x; nit = 0; }
+      const uint8_t* nvol = nit == 0 && p + 1 < P ? item_volts(a, nitem, nant) : ivol;
       tc::named_sync(1, 128);                         // phase B of p-1 done: raw[(p+1)&1] free
-      if (p + 1 < P) stage(nitem, nit, raw0 + ((p + 1) & 1) * rawsz);
+      if (p + 1 < P) stage(nvol, nit, raw0 + ((p + 1) & 1) * rawsz);
       cp_async_commit();
       cp_async_wait<1>();
       const int b = (int)(p & 1);
@@ -672,6 +673,7 @@ __global__ void __launch_bounds__(tcp::NT, 2) beams_tc_pipe_kernel(const TcArgs 
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(bars + tcp::A1F + b);
       item = nitem;
+      ivol = nvol;
       it = nit;
     }
     cp_async_wait<0>();
@@ -844,13 +846,14 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const BeamArgs& a = ta.b;
   if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
-  // The serial kernel (four CTAs per SM, every warp in every phase) measures faster than
+  // The serial kernel (several CTAs per SM, every warp in every phase) measures faster than
   // the warp-specialised pipeline on the 4x256 lattice; FFTBF_TC_PIPE=1 selects the latter.
   const char* pipe = getenv("FFTBF_TC_PIPE");
   if (ta.split || !(pipe && pipe[0] && pipe[0] != '0')) {   // the split form is serial only
     const TcSmem L = tc_smem_layout(a.nx * a.ny, ta.split != 0, ta.w4 != 0);
     // at most 8 CTAs of 64 TMEM columns per SM: keep a ninth from fitting (registers and
-    // this shared memory hold it at 5 on the 4x256 lattice, 3 for the split form)
+    // shared memory hold it at 6 on the 4x256 lattice for FP16 with real weights, 5 for
+    // BF16, 3 for the split form)
     size_t smem = (size_t)L.total;
     if (smem < 26 * 1024) smem = 26 * 1024;
     if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");

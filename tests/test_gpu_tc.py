@@ -66,6 +66,8 @@ SHAPES = [
     ((4, 256, 4, 512, 2, 3, 768, 384), "half_sine"),    # CHIME-like lattice
     ((4, 256, 4, 512, 1, 2, 30, 5), "random"),          # one pol, ragged: 5 snapshots, 2 per step
     ((3, 200, 4, 512, 2, 2, 32, 16), "random"),         # E-W padded 3 -> 4, 200 N-S feeds
+    ((4, 200, 4, 512, 2, 2, 32, 16), "half_sine"),      # real weights, rows of 200 feeds
+    ((4, 160, 4, 512, 1, 2, 16, 8), "half_sine"),       # real weights, rows of 160 feeds
 ]
 
 
