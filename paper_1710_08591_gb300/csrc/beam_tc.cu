@@ -174,13 +174,17 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 
 // SPLIT (FP16 only): every operand is an FP16 value and its FP16 residual, and each stage
 // is hi*hi + hi*lo + lo*hi accumulated in FP32, which gives the result FP32 accuracy.
-template <bool BF16, bool SPLIT = false>
+// NY256 (FP16 form with real weights on the 4x256 lattice, 16-byte aligned voltages): the
+// lattice sizes and the input-stage path are constants.
+template <bool BF16, bool SPLIT = false, bool NY256 = false>
 __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
-  const int nant = a.nx * a.ny;
-  const TcSmem L = tc_smem_layout(nant, SPLIT, ta.w4 != 0);
+  const int ny = NY256 ? 256 : a.ny;
+  const int nant = NY256 ? 1024 : a.nx * a.ny;
+  const bool w4 = NY256 || ta.w4 != 0;
+  const TcSmem L = tc_smem_layout(nant, SPLIT, w4);
   unsigned char* a1 = smem + L.a1;
   unsigned char* a2 = smem + L.a2;
   unsigned char* b1s = smem + L.b1;
@@ -217,7 +221,8 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   }
   // FP16 form: packed-half input stage when the E-W axis is a plain 4-point DFT over
   // groups of four N-S feeds (4-byte words), and packed-half twiddles between the stages.
-  const bool fast16 = !BF16 && !SPLIT && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny;
+  const bool fast16 =
+      NY256 || (!BF16 && !SPLIT && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny);
   if constexpr (!BF16 && !SPLIT) {
     uint2* tw16 = reinterpret_cast<uint2*>(twsm);      // [k1][n2] {(c, d), (-d, c)}
     for (int i = tid; i < 512; i += tcl::NT) {
@@ -227,14 +232,14 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   } else {
     for (int i = tid; i < 512; i += tcl::NT) twsm[i] = a.tw[(i >> 4) * (i & 15)];
   }
-  if (fast16 && ta.w4) {
+  if (fast16 && w4) {
     // real weights: per feed (scale w / 16, scale w), (16 re, im) -> scale (re + i im) w
     uint32_t* w16r = reinterpret_cast<uint32_t*>(wsm);
     const float sc = ta.scale;
     for (int i = tid; i < nant; i += tcl::NT) {
       const float w = a.w[i].x;
-      const int ix = i / a.ny, iy = i - ix * a.ny;
-      w16r[ix * a.ny + w4_pos(iy, a.ny)] = pack2<false>(w * sc * 0.0625f, w * sc);
+      const int ix = i / ny, iy = i - ix * ny;
+      w16r[ix * ny + w4_pos(iy, ny)] = pack2<false>(w * sc * 0.0625f, w * sc);
     }
   } else if (fast16) {
     // per feed {scale w / 16, scale i w}: (16 re, im) -> scale (re + i im) w
@@ -254,7 +259,8 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   tc::fence_after_sync();
   const uint32_t tbase = *taddr_sm;
   const uint32_t tlane = (uint32_t)(32 * warp) << 16;        // this warp's TMEM lane quarter
-  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const bool vec16 =
+      NY256 || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
   const uint32_t id1 = tc::idesc_f16(128, 64, BF16);
   const uint32_t id2 = tc::idesc_f16(128, 32, BF16);
   const float inv_s2 = 1.0f / (ta.scale * ta.scale);
@@ -303,11 +309,11 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
     // ---- unpack x weight, E-W DFT, scale, round: stage-1 operand A1[(s,A,n2)][(n1,c)]
     const unsigned char* raw = raw0 + cur * rawsz;
     if (fast16) {
-      if (ta.w4)
-        input_stage16<true>(a1, raw, wsm, nant, a.ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
+      if (w4)
+        input_stage16<true>(a1, raw, wsm, nant, ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
                             tcl::A1_SBO);
       else
-        input_stage16<false>(a1, raw, wsm, nant, a.ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
+        input_stage16<false>(a1, raw, wsm, nant, ny, tid, 2 * it + 1 < nsnap, tcl::A1_LBO,
                              tcl::A1_SBO);
     } else
 #pragma unroll
@@ -857,8 +863,12 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
     size_t smem = (size_t)L.total;
     if (smem < 26 * 1024) smem = 26 * 1024;
     if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
+    const bool ny256 = !ta.split && !ta.bf16 && ta.w4 && a.ew_dft && a.nx == 4 && a.ny == 256 &&
+                       a.nyf == 256 && (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
     auto kern = ta.split ? beams_tc_kernel<false, true>
-                         : (ta.bf16 ? beams_tc_kernel<true, false> : beams_tc_kernel<false, false>);
+                         : (ta.bf16 ? beams_tc_kernel<true, false>
+                                    : (ny256 ? beams_tc_kernel<false, false, true>
+                                             : beams_tc_kernel<false, false>));
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         cudaSharedmemCarveoutMaxShared));
