@@ -174,16 +174,18 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 
 // SPLIT (FP16 only): every operand is an FP16 value and its FP16 residual, and each stage
 // is hi*hi + hi*lo + lo*hi accumulated in FP32, which gives the result FP32 accuracy.
-// NY256 (FP16 form with real weights on the 4x256 lattice, 16-byte aligned voltages): the
-// lattice sizes and the input-stage path are constants.
+// NY256 (the 4x256 lattice with a 4-point E-W DFT and 16-byte aligned voltages; for the
+// FP16 form also real weights): the lattice sizes and the input-stage path are constants.
 template <bool BF16, bool SPLIT = false, bool NY256 = false>
 __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
   const int ny = NY256 ? 256 : a.ny;
+  const int nyf = NY256 ? 256 : a.nyf;
   const int nant = NY256 ? 1024 : a.nx * a.ny;
-  const bool w4 = NY256 || ta.w4 != 0;
+  constexpr bool FP16W4 = NY256 && !BF16 && !SPLIT;
+  const bool w4 = FP16W4 || ta.w4 != 0;
   const TcSmem L = tc_smem_layout(nant, SPLIT, w4);
   unsigned char* a1 = smem + L.a1;
   unsigned char* a2 = smem + L.a2;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
   // FP16 form: packed-half input stage when the E-W axis is a plain 4-point DFT over
   // groups of four N-S feeds (4-byte words), and packed-half twiddles between the stages.
   const bool fast16 =
-      NY256 || (!BF16 && !SPLIT && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny);
+      FP16W4 || (!BF16 && !SPLIT && a.ew_dft && a.nx == 4 && (a.ny & 3) == 0 && a.nyf == a.ny);
   if constexpr (!BF16 && !SPLIT) {
     uint2* tw16 = reinterpret_cast<uint2*>(twsm);      // [k1][n2] {(c, d), (-d, c)}
     for (int i = tid; i < 512; i += tcl::NT) {
@@ -321,12 +323,22 @@ __global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_
       const int c = tid + q * tcl::NT;
       const int s = c >> 8, iy = c & 255;
       float2 z[4] = {czero(), czero(), czero(), czero()};
-      if (iy < a.nyf && 2 * it + s < nsnap) {
+      if (iy < nyf && 2 * it + s < nsnap) {
         const unsigned char* rs = raw + s * nant;
-        if (a.ew_dft) {
+        if (NY256 || a.ew_dft) {
+          if (a.real_w) {
+            // real weights: two multiplies, the same roundings as the complex product
 #pragma unroll
-          for (int ix = 0; ix < 4; ++ix)
-            z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+            for (int ix = 0; ix < 4; ++ix) {
+              const float wr = wsm[ix * ny + iy].x;
+              const float2 xv = unpack_byte(rs[ix * ny + iy]);
+              z[ix] = make_float2(wr * xv.x, wr * xv.y);
+            }
+          } else {
+#pragma unroll
+            for (int ix = 0; ix < 4; ++ix)
+              z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
+          }
           Dft<4>::run(z);
         } else {
           for (int ix = 0; ix < a.nx; ++ix) {
@@ -863,10 +875,11 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
     size_t smem = (size_t)L.total;
     if (smem < 26 * 1024) smem = 26 * 1024;
     if (smem > 200 * 1024) return set_error(FFTBF_EUNSUPPORTED, "tensor-core form: lattice too large");
-    const bool ny256 = !ta.split && !ta.bf16 && ta.w4 && a.ew_dft && a.nx == 4 && a.ny == 256 &&
+    const bool ny256 = (ta.split || ta.bf16 || ta.w4) && a.ew_dft && a.nx == 4 && a.ny == 256 &&
                        a.nyf == 256 && (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
-    auto kern = ta.split ? beams_tc_kernel<false, true>
-                         : (ta.bf16 ? beams_tc_kernel<true, false>
+    auto kern = ta.split ? (ny256 ? beams_tc_kernel<false, true, true> : beams_tc_kernel<false, true>)
+                         : (ta.bf16 ? (ny256 ? beams_tc_kernel<true, false, true>
+                                             : beams_tc_kernel<true, false>)
                                     : (ny256 ? beams_tc_kernel<false, false, true>
                                              : beams_tc_kernel<false, false>));
     FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
