@@ -40,18 +40,29 @@ constexpr WarpVariant kWarpVariants[] = {{4, 512}, {8, 128}, {2, 1024}, {3, 256}
 constexpr int kNumWarpVariants = sizeof(kWarpVariants) / sizeof(kWarpVariants[0]);
 }  // namespace bt
 
+// Each warp-path item runs the constant-size instance when its lattice is exactly the
+// variant's shape with 2x N-S padding (warp_full), the runtime-size one otherwise.
 template <int MX, int R>
 __device__ __noinline__ void batch_warp_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                              bool load_tables) {
-  warp_item<MX, R>(a, item, smem, load_tables);
+  if (warp_full(a, 16 * R))
+    warp_item<MX, R, true>(a, item, smem, load_tables);
+  else
+    warp_item<MX, R>(a, item, smem, load_tables);
 }
 __device__ __noinline__ void batch_warp2_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                               bool load_tables) {
-  warp2_item<1>(a, item, smem, load_tables);
+  if (warp_full(a, 1024))
+    warp2_item<1, true>(a, item, smem, load_tables);
+  else
+    warp2_item<1>(a, item, smem, load_tables);
 }
 __device__ __noinline__ void batch_lane16_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                                bool load_tables) {
-  lane_item16(a, item, smem, load_tables);
+  if (warp_full(a, 16))
+    lane_item16<true>(a, item, smem, load_tables);
+  else
+    lane_item16(a, item, smem, load_tables);
 }
 
 
@@ -298,6 +309,7 @@ static void fill_args(const fftbf_plan* p, BeamArgs& a) {
   a.npol = p->npol; a.nfreq = p->nfreq; a.n_int = p->n_int;
   a.nyf = std::min(p->ny, p->my);
   a.ew_dft = (p->mx == p->nx) && (p->mx & (p->mx - 1)) == 0 && p->mx <= 16;
+  a.real_w = p->real_w ? 1 : 0;
 }
 
 static int launch_jobs(fftbf_batch* bb, int64_t total, cudaStream_t st) {

@@ -6,13 +6,13 @@
 
 namespace fftbf {
 
-template <int MX, int R>
+template <int MX, int R, bool FULL>
 __global__ void __launch_bounds__(kThreads, 2) beams_fp32_warp_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nitems = a.nwin * a.nfreq;
   bool load = true;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    warp_item<MX, R>(a, item, smem, load);
+    warp_item<MX, R, FULL>(a, item, smem, load);
     load = false;
   }
 }
@@ -22,7 +22,8 @@ static int launch_warp(const BeamArgs& a0, int nsm, cudaStream_t st) {
   BeamArgs a = a0;
   a.S = WarpCfg<MX, R>::S;
   const size_t smem = warp_item_smem(a.S, a.mx, a.nx, a.ny, R);
-  auto kern = beams_fp32_warp_kernel<MX, R>;
+  auto kern = warp_full(a, 16 * R) ? beams_fp32_warp_kernel<MX, R, true>
+                                    : beams_fp32_warp_kernel<MX, R, false>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));
@@ -36,23 +37,24 @@ static int launch_warp(const BeamArgs& a0, int nsm, cudaStream_t st) {
   return FFTBF_OK;
 }
 
-template <int MX>
+template <int MX, bool FULL>
 __global__ void __launch_bounds__(kThreads, 2) beams_fp32_warp2_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nitems = a.nwin * a.nfreq;
   bool load = true;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    warp2_item<MX>(a, item, smem, load);
+    warp2_item<MX, FULL>(a, item, smem, load);
     load = false;
   }
 }
 
+template <bool FULL>
 __global__ void __launch_bounds__(kThreads, 2) beams_fp32_lane16_kernel(const BeamArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nitems = a.nwin * a.nfreq;
   bool load = true;
   for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-    lane_item16(a, item, smem, load);
+    lane_item16<FULL>(a, item, smem, load);
     load = false;
   }
 }
@@ -112,13 +114,19 @@ int launch_beams_fp32_warp(const BeamArgs& a0, int nsm, cudaStream_t st) {
     BeamArgs a = a0;
     a.S = 4 / a.mx;
     const size_t smem = warp2_item_smem(a.S, a.mx, a.nx, a.ny);
-    if (a.mx == 1) return launch_item_kernel(beams_fp32_warp2_kernel<1>, a, smem, nsm, st);
-    return launch_item_kernel(beams_fp32_warp2_kernel<2>, a, smem, nsm, st);
+    const bool full = warp_full(a, 1024);
+    if (a.mx == 1)
+      return launch_item_kernel(full ? beams_fp32_warp2_kernel<1, true> : beams_fp32_warp2_kernel<1, false>,
+                                a, smem, nsm, st);
+    return launch_item_kernel(full ? beams_fp32_warp2_kernel<2, true> : beams_fp32_warp2_kernel<2, false>,
+                              a, smem, nsm, st);
   }
   if (a0.my == 32) {
     BeamArgs a = a0;
     a.S = kLaneS;
-    return launch_item_kernel(beams_fp32_lane16_kernel, a, lane_item_smem(a.nx, a.ny), nsm, st);
+    return launch_item_kernel(warp_full(a, 16) ? beams_fp32_lane16_kernel<true>
+                                               : beams_fp32_lane16_kernel<false>,
+                              a, lane_item_smem(a.nx, a.ny), nsm, st);
   }
   const BeamArgs& a = a0;
   switch (a.mx) {

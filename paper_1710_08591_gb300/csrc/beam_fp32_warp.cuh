@@ -69,35 +69,53 @@ template <int MX, int R> struct WarpCfg {
   static constexpr int H = 32 / D;                      // k1 classes per n2
 };
 
+// FULL: the lattice is MX x NH feeds, all live, with an MX-point E-W DFT (the radix-3
+// butterfly for MX = 3) and 16-byte aligned voltages, i.e. exactly 2x N-S padding: its
+// sizes are compile-time constants.
+__host__ __device__ inline bool warp_full(const BeamArgs& a, int nh) {
+  return a.nx == a.mx && a.ny == nh && a.nyf == nh && (a.ew_dft || a.mx == 3) &&
+         (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
+}
+
+// Weight x unpacked byte; real weights in two multiplies (the same roundings as the complex
+// product with a zero imaginary part).
+__device__ __forceinline__ float2 weigh(bool real_w, float2 w, uint8_t b) {
+  const float2 x = unpack_byte(b);
+  return real_w ? make_float2(w.x * x.x, w.x * x.y) : cmul(w, x);
+}
+
 // Unpack x weight and E-W transform of S snapshots into per-transform regions:
 // region (s MX + A), slot (iy mod R) + stride (iy / R), for the feeds iy < NH (zeros
 // past nyf and past the last snapshot).
-template <int MX, int R, int NH>
+template <int MX, int R, int NH, bool FULL = false>
 __device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* raw, int S, int it,
                                               int nsnap, int nant, const float2* wsm,
                                               const float2* exsm, float2* regs, int reg,
                                               int stride) {
+  const int ny = FULL ? NH : a.ny;
+  const int nyf = FULL ? NH : a.nyf;
+  const bool rw = a.real_w != 0;
   for (int c = threadIdx.x; c < S * NH; c += kThreads) {
     const int s = c / NH, iy = c - s * NH;
     float2 z[MX];
 #pragma unroll
     for (int A = 0; A < MX; ++A) z[A] = czero();
-    if (iy < a.nyf && it * S + s < nsnap) {
+    if (iy < nyf && it * S + s < nsnap) {
       const uint8_t* rs = raw + s * nant;
       if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8 || MX == 16) {
-        if (a.ew_dft) {
+        if (FULL || a.ew_dft) {
 #pragma unroll
-          for (int ix = 0; ix < MX; ++ix) z[ix] = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+          for (int ix = 0; ix < MX; ++ix) z[ix] = weigh(rw, wsm[ix * ny + iy], rs[ix * ny + iy]);
           Dft<MX>::run(z);
         }
       }
       bool done = false;
       if constexpr (MX == 3) {
-        if (a.nx == 3) {
+        if (FULL || a.nx == 3) {
           // 3-point DFT: X_{1,2} = z0 - (z1 + z2)/2 -/+ i (sqrt(3)/2)(z1 - z2)
-          const float2 z0 = cmul(wsm[iy], unpack_byte(rs[iy]));
-          const float2 z1 = cmul(wsm[a.ny + iy], unpack_byte(rs[a.ny + iy]));
-          const float2 z2 = cmul(wsm[2 * a.ny + iy], unpack_byte(rs[2 * a.ny + iy]));
+          const float2 z0 = weigh(rw, wsm[iy], rs[iy]);
+          const float2 z1 = weigh(rw, wsm[ny + iy], rs[ny + iy]);
+          const float2 z2 = weigh(rw, wsm[2 * ny + iy], rs[2 * ny + iy]);
           const float2 sm = cadd(z1, z2), df = csub(z1, z2);
           const float h3 = 0.86602540378443865f;
           const float2 m = make_float2(z0.x - 0.5f * sm.x, z0.y - 0.5f * sm.y);
@@ -108,9 +126,9 @@ __device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* 
           done = true;
         }
       }
-      if (!a.ew_dft && !done) {
+      if (!FULL && !a.ew_dft && !done) {
         for (int ix = 0; ix < a.nx; ++ix) {
-          const float2 col = cmul(wsm[ix * a.ny + iy], unpack_byte(rs[ix * a.ny + iy]));
+          const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
 #pragma unroll
           for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
         }
@@ -131,13 +149,14 @@ __host__ __device__ inline size_t warp_item_smem(int S, int mx, int nx, int ny, 
 }
 
 // One work item (window, channel): all its snapshots, S per step, bytes double-buffered
-// through cp.async. 256 threads. a.S must be WarpCfg<MX, R>::S and a.nyf <= N/2.
-template <int MX, int R>
+// through cp.async. 256 threads. a.S must be WarpCfg<MX, R>::S and a.nyf <= N/2; FULL
+// only where warp_full(a, N/2) holds.
+template <int MX, int R, bool FULL = false>
 __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                           bool load_tables) {
   using C = WarpCfg<MX, R>;
   constexpr int N = C::N, S = C::S, J = C::J, REG = C::REG, D = C::D, H = C::H;
-  const int nant = a.nx * a.ny;
+  const int nant = FULL ? MX * (N / 2) : a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
   float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
   float2* exsm = wsm + nant;
@@ -147,7 +166,8 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nsnap = a.n_int * a.npol;
   const int niter = (nsnap + S - 1) / S;
-  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const bool vec16 =
+      FULL || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
   if (load_tables) {
     for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
     for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
@@ -169,7 +189,7 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
     cp_async_wait<1>();
     __syncthreads();                                  // bytes of `it` visible; regions free
     // ---- unpack x weight, E-W transform -> region (s MX + A), slot (iy mod R) + (R+1)(iy / R)
-    warp_ew_stage<MX, R, N / 2>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
+    warp_ew_stage<MX, R, N / 2, FULL>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
                                 REG, R + 1);
     __syncthreads();                                  // regions written
 #pragma unroll
@@ -263,12 +283,12 @@ __host__ __device__ inline size_t warp2_item_smem(int S, int mx, int nx, int ny)
                                        (size_t)S * mx * 32 * 65);
 }
 
-template <int MX>
+template <int MX, bool FULL = false>
 __device__ __forceinline__ void warp2_item(const BeamArgs& a, int64_t item, unsigned char* smem,
                                            bool load_tables) {
   using C = Warp2Cfg<MX>;
   constexpr int N = C::N, R = C::R, S = C::S, REG = C::REG;
-  const int nant = a.nx * a.ny;
+  const int nant = FULL ? MX * 1024 : a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
   float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
   float2* exsm = wsm + nant;
@@ -280,7 +300,8 @@ __device__ __forceinline__ void warp2_item(const BeamArgs& a, int64_t item, unsi
   const int pair = warp >> 1, g = warp & 1;
   const int nsnap = a.n_int * a.npol;
   const int niter = (nsnap + S - 1) / S;
-  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const bool vec16 =
+      FULL || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
   if (load_tables) {
     for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
     for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
@@ -301,7 +322,7 @@ __device__ __forceinline__ void warp2_item(const BeamArgs& a, int64_t item, unsi
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    warp_ew_stage<MX, R, N / 2>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
+    warp_ew_stage<MX, R, N / 2, FULL>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs,
                                 REG, R + 1);
     __syncthreads();
     float2* rg = regs + pair * REG;          // transform `pair` of this step
@@ -365,10 +386,11 @@ __host__ __device__ inline size_t lane_item_smem(int nx, int ny) {
   return 2 * rawsz + sizeof(float2) * (nant + (size_t)16 * nx + (size_t)kLaneS * 16 * 17);
 }
 
+template <bool FULL = false>
 __device__ __forceinline__ void lane_item16(const BeamArgs& a, int64_t item, unsigned char* smem,
                                             bool load_tables) {
   constexpr int MX = 16, N = 32, S = kLaneS, REG = 17;
-  const int nant = a.nx * a.ny;
+  const int nant = FULL ? 256 : a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
   float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
   float2* exsm = wsm + nant;
@@ -376,7 +398,8 @@ __device__ __forceinline__ void lane_item16(const BeamArgs& a, int64_t item, uns
   const int t = threadIdx.x;               // transform (s, A) = (t / 16, t % 16)
   const int nsnap = a.n_int * a.npol;
   const int niter = (nsnap + S - 1) / S;
-  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
+  const bool vec16 =
+      FULL || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
   if (load_tables) {
     for (int i = threadIdx.x; i < nant; i += kThreads) wsm[i] = a.w[i];
     for (int i = threadIdx.x; i < MX * a.nx; i += kThreads) exsm[i] = a.ex[i];
@@ -392,7 +415,7 @@ __device__ __forceinline__ void lane_item16(const BeamArgs& a, int64_t item, uns
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    warp_ew_stage<MX, 16, 16>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs, REG, 17);
+    warp_ew_stage<MX, 16, 16, FULL>(a, smem + (it & 1) * rawsz, S, it, nsnap, nant, wsm, exsm, regs, REG, 17);
     __syncthreads();
     float2 x[16];
 #pragma unroll

@@ -176,8 +176,12 @@ __device__ __forceinline__ void load_kmajor(unsigned char* dst, const uint16_t* 
 // is hi*hi + hi*lo + lo*hi accumulated in FP32, which gives the result FP32 accuracy.
 // NY256 (the 4x256 lattice with a 4-point E-W DFT and 16-byte aligned voltages; for the
 // FP16 form also real weights): the lattice sizes and the input-stage path are constants.
+#ifndef FFTBF_TC16_MIN_BLOCKS
+#define FFTBF_TC16_MIN_BLOCKS 6     // CTAs per SM the FP16 form's register budget targets
+#endif
 template <bool BF16, bool SPLIT = false, bool NY256 = false>
-__global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : 6)) beams_tc_kernel(const TcArgs ta) {
+__global__ void __launch_bounds__(tcl::NT, SPLIT ? 3 : (BF16 ? 5 : FFTBF_TC16_MIN_BLOCKS))
+beams_tc_kernel(const TcArgs ta) {
   const BeamArgs& a = ta.b;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
