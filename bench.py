@@ -60,7 +60,7 @@ def flops_per_snapshot(nx, ny, mx, my):
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_FP32 = 16 * (403.112448e6 + 3.731200e6)
+TRAFFIC_FP32 = None
 
 
 def samples_per_step():

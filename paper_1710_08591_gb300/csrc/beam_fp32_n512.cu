@@ -21,7 +21,9 @@
 namespace fftbf {
 
 namespace n512 {
-constexpr int kRegion = 32 * 17;   // float2 slots per transform region (X1 tile, padded)
+constexpr int kRow = 17;           // float2 row stride of the input and X1 tiles
+constexpr int kRegion = 32 * kRow; // float2 slots per transform region (X1 tile, padded)
+__device__ __forceinline__ int in_slot(int iy) { return (iy & 15) + kRow * (iy >> 4); }
 }
 
 #ifndef FFTBF_N512_NW
@@ -44,11 +46,12 @@ beams_fp32_n512_kernel(const BeamArgs a) {
   const int nyf = NY256 ? 256 : a.nyf;
   const int nant = NY256 ? MX * 256 : a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
-  float2* wsm = reinterpret_cast<float2*>(smem + 2 * rawsz);
-  float2* exsm = wsm + nant;
-  float2* tw512 = exsm + MX * a.nx;          // [32 k1][16 n2] = W512^(n2 k1)
+  // tables and regions first, so the weights start 16-byte aligned (128-bit loads)
+  float2* tw512 = reinterpret_cast<float2*>(smem + 2 * rawsz);  // [32 k1][16 n2] = W512^(n2 k1)
   float2* tw32 = tw512 + 512;                // [2 h][16 n1]  = W32^(h n1)
   float2* reg = tw32 + 32;                   // [NW][kRegion]
+  float2* wsm = reg + NW * n512::kRegion;
+  float2* exsm = wsm + nant;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nsnap = a.n_int * a.npol;
@@ -109,45 +112,74 @@ beams_fp32_n512_kernel(const BeamArgs a) {
     if (has_next) stage(nvol, nit, cur ^ 1);
     cp_async_commit();
 
-    // ---- unpack x weight, E-W transform -> Z[s*MX + A][pad16(iy)]
+    // ---- unpack x weight, E-W transform -> Z[s*MX + A][in_slot(iy)]
     const uint8_t* raw = smem + cur * rawsz;
-#pragma unroll(NY256 ? S * 256 / NT : 1)
-    for (int r = 0, c = threadIdx.x; NY256 ? r < S * 256 / NT : c < S * 256; ++r, c += NT) {
-      const int s = c >> 8, iy = c & 255;
-      float2 z[MX];
+    if constexpr (NY256) {
+      // one snapshot, two adjacent feeds per thread: 16-bit byte loads and 128-bit weight
+      // loads
+      static_assert(MX == 4 && S == 1 && 2 * NT == 256, "one feed pair per thread");
+      const int iy = 2 * threadIdx.x;
+      float2 z0[4], z1[4];
 #pragma unroll
-      for (int A = 0; A < MX; ++A) z[A] = czero();
-      if (iy < nyf && it * S + s < nsnap) {
-        const uint8_t* rs = raw + s * nant;
-        if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
-          if (NY256 || a.ew_dft) {
-            if (a.real_w) {
-              // real weights: w x in two multiplies (the same roundings as the complex
-              // product with a zero imaginary part)
-#pragma unroll
-              for (int ix = 0; ix < MX; ++ix) {
-                const float wr = wsm[ix * ny + iy].x;
-                const float2 xv = unpack_byte(rs[ix * ny + iy]);
-                z[ix] = make_float2(wr * xv.x, wr * xv.y);
-              }
-            } else {
-#pragma unroll
-              for (int ix = 0; ix < MX; ++ix)
-                z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
-            }
-            Dft<MX>::run(z);
-          }
-        }
-        if (!NY256 && !a.ew_dft) {
-          for (int ix = 0; ix < a.nx; ++ix) {
-            const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
-#pragma unroll
-            for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
-          }
+      for (int ix = 0; ix < 4; ++ix) {
+        const unsigned v = *reinterpret_cast<const uint16_t*>(raw + ix * 256 + iy);
+        const float4 w = *reinterpret_cast<const float4*>(wsm + ix * 256 + iy);
+        const float2 x0 = unpack_byte(v & 255u), x1 = unpack_byte(v >> 8);
+        if (a.real_w) {
+          // real weights: two multiplies (the roundings of the complex product)
+          z0[ix] = make_float2(w.x * x0.x, w.x * x0.y);
+          z1[ix] = make_float2(w.z * x1.x, w.z * x1.y);
+        } else {
+          z0[ix] = cmul(make_float2(w.x, w.y), x0);
+          z1[ix] = cmul(make_float2(w.z, w.w), x1);
         }
       }
+      Dft<4>::run(z0);
+      Dft<4>::run(z1);
+      const int sl = n512::in_slot(iy);      // iy + 1 is the next slot (iy even)
 #pragma unroll
-      for (int A = 0; A < MX; ++A) reg[(s * MX + A) * n512::kRegion + pad16(iy)] = z[A];
+      for (int A = 0; A < 4; ++A) {
+        reg[A * n512::kRegion + sl] = z0[A];
+        reg[A * n512::kRegion + sl + 1] = z1[A];
+      }
+    } else {
+      for (int c = threadIdx.x; c < S * 256; c += NT) {
+        const int s = c >> 8, iy = c & 255;
+        float2 z[MX];
+#pragma unroll
+        for (int A = 0; A < MX; ++A) z[A] = czero();
+        if (iy < nyf && it * S + s < nsnap) {
+          const uint8_t* rs = raw + s * nant;
+          if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
+            if (a.ew_dft) {
+              if (a.real_w) {
+                // real weights: w x in two multiplies (the same roundings as the complex
+                // product with a zero imaginary part)
+#pragma unroll
+                for (int ix = 0; ix < MX; ++ix) {
+                  const float wr = wsm[ix * ny + iy].x;
+                  const float2 xv = unpack_byte(rs[ix * ny + iy]);
+                  z[ix] = make_float2(wr * xv.x, wr * xv.y);
+                }
+              } else {
+#pragma unroll
+                for (int ix = 0; ix < MX; ++ix)
+                  z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
+              }
+              Dft<MX>::run(z);
+            }
+          }
+          if (!a.ew_dft) {
+            for (int ix = 0; ix < a.nx; ++ix) {
+              const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
+#pragma unroll
+              for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
+            }
+          }
+        }
+#pragma unroll
+        for (int A = 0; A < MX; ++A) reg[(s * MX + A) * n512::kRegion + n512::in_slot(iy)] = z[A];
+      }
     }
     __syncthreads();                                  // (B) regions written
 
@@ -155,13 +187,13 @@ beams_fp32_n512_kernel(const BeamArgs a) {
     {
       float2 x[16];
 #pragma unroll
-      for (int n1 = 0; n1 < 16; ++n1) x[n1] = cmul(myreg[n2 + 17 * n1], tw32[h * 16 + n1]);
+      for (int n1 = 0; n1 < 16; ++n1) x[n1] = cmul(myreg[n2 + n512::kRow * n1], tw32[h * 16 + n1]);
       Dft<16>::run(x);
       __syncwarp();
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k1 = 2 * m + h;
-        myreg[k1 * 17 + n2] = cmul(x[m], tw512[k1 * 16 + n2]);
+        myreg[k1 * n512::kRow + n2] = cmul(x[m], tw512[k1 * 16 + n2]);
       }
       __syncwarp();
     }
@@ -169,7 +201,7 @@ beams_fp32_n512_kernel(const BeamArgs a) {
     {
       float2 y[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) y[q] = myreg[lane * 17 + q];
+      for (int q = 0; q < 16; ++q) y[q] = myreg[lane * n512::kRow + q];
       Dft<16>::run(y);
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) acc[k2] = fmaf(y[k2].x, y[k2].x, fmaf(y[k2].y, y[k2].y, acc[k2]));
@@ -209,8 +241,8 @@ beams_fp32_n512_kernel(const BeamArgs a) {
 static size_t n512_smem_bytes(const BeamArgs& a, int S, int NW) {
   const int nant = a.nx * a.ny;
   const size_t rawsz = ((size_t)S * nant + 15) & ~(size_t)15;
-  return 2 * rawsz + sizeof(float2) * ((size_t)nant + (size_t)a.mx * a.nx + 512 + 32 +
-                                       (size_t)NW * n512::kRegion);
+  return 2 * rawsz + sizeof(float2) * (512 + 32 + (size_t)NW * n512::kRegion +
+                                       (size_t)nant + (size_t)a.mx * a.nx);
 }
 
 template <int MX>
