@@ -60,7 +60,10 @@ def flops_per_snapshot(nx, ny, mx, my):
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_FP32 = None
+TRAFFIC_FP32 = 16 * (403.262208e6 + 3.753472e6)
+# The same for one batched step (one batch_kernel launch over 8192 samples), from the
+# 512-sample profile case (`--workload batched --profile-case`) scaled x16.
+TRAFFIC_BATCH = 16 * (2188.590e6 + 47.181056e6)
 
 
 def samples_per_step():
@@ -328,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = flops / (k_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_FP32,
-                "kernel": "beams_fp32_n512_kernel<4>", "ms_per_launch": k_ms,
+                "kernel": "beams_fp32_n512_kernel<4, true>", "ms_per_launch": k_ms,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
                         "peak_gbs": peaks["hbm_gbs"],
@@ -596,7 +599,7 @@ def run_batched(args):
             "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-                         "traffic": None, "kernel": "batch_kernel",
+                         "traffic": TRAFFIC_BATCH, "kernel": "batch_kernel",
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                          "hbm": {"achieved_gbs": byts / (ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
                                  "frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
