@@ -86,6 +86,34 @@ def test_batch_bit_identical_alone_and_in_mix_and_replayed():
         assert np.array_equal(alone[0], mix[k])
 
 
+def test_batch_constant_size_and_runtime_instances_bit_identical():
+    """Aligned voltages run the constant-size instances of the exactly 2x-padded shapes
+    (all six lattices), voltages 3 bytes off the 16-byte boundary the runtime-size ones:
+    the beams must be bit-identical."""
+    T, n_int = 32, 16
+    arrs = _arrays([2, 2, 2, 2, 1, 2], T, n_int, seed=90)
+    res = []
+    for off in (0, 3):
+        plans = [fb.plan_create(*a["shape"], weights=a["w"]) for a in arrs]
+        dvs = []
+        for a in arrs:
+            flat = torch.from_numpy(np.ascontiguousarray(a["v"]).reshape(-1))
+            base = torch.zeros(flat.numel() + 16, dtype=torch.uint8, device="cuda")
+            base[off:off + flat.numel()].copy_(flat)
+            dvs.append(base[off:off + flat.numel()])
+        outs = [torch.full((T // a["shape"][6], a["shape"][5], a["shape"][2], a["shape"][3]),
+                           float("nan"), device="cuda") for a in arrs]
+        with fb.batch_create(plans) as b:
+            fb.batch_execute(b, dvs, T, outs, None)
+            torch.cuda.synchronize()
+        res.append([o.cpu().numpy() for o in outs])
+        for p_ in plans:
+            p_.close()
+    for k, (x, y) in enumerate(zip(*res)):
+        assert np.all(np.isfinite(x)), arrs[k]["shape"]
+        assert np.array_equal(x, y), arrs[k]["shape"]
+
+
 def test_batch_rejects_unsupported_shape():
     with fb.plan_create(5, 12, 5, 24, 1, 2, 4) as p:
         with pytest.raises(fb.FftbfError) as e:

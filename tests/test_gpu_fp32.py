@@ -216,10 +216,16 @@ def test_tied_rejects_off_grid_pointing():
 
 @pytest.mark.parametrize("shape,prec", [((4, 256, 4, 512, 2, 2, 32, 16), "fp32"),
                                         ((3, 128, 3, 256, 2, 2, 32, 16), "fp32"),
-                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16")])
+                                        ((8, 64, 8, 128, 2, 2, 32, 16), "fp32"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_bf16"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16x3")])
 def test_misaligned_voltages_give_identical_beams(shape, prec):
     """A voltage pointer off the 16-byte boundary is accepted (staged byte by byte instead
-    of with 16-byte copies) and gives bit-identical beams."""
+    of with 16-byte copies) and gives bit-identical beams. The aligned call runs the
+    constant-size instance of the 4x256 lattice (or of an exactly 2x-padded warp-path
+    shape), the misaligned one the runtime-size instance, so this also checks that both
+    sum in the same order."""
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=77)
     flat = torch.from_numpy(np.ascontiguousarray(v).reshape(-1))
@@ -229,8 +235,9 @@ def test_misaligned_voltages_give_identical_beams(shape, prec):
         base[off:off + flat.numel()].copy_(flat)
         out = torch.full((T // n_int, nfreq, mx, my), float("nan"), device="cuda")
         with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
-            if prec == "tc_fp16":
-                fb.plan_set_precision(plan, fb.PREC_TC_FP16)
+            if prec != "fp32":
+                fb.plan_set_precision(plan, {"tc_fp16": fb.PREC_TC_FP16, "tc_bf16": fb.PREC_TC_BF16,
+                                             "tc_fp16x3": fb.PREC_TC_FP16X3}[prec])
             fb.execute(plan, base[off:off + flat.numel()], T, out)
             fb.plan_sync(plan)
         outs.append(out.cpu().numpy())
