@@ -217,6 +217,115 @@ __global__ void __launch_bounds__(256) stacked_vis_fft_kernel(const float* __res
   cp_async_wait<0>();
 }
 
+
+// Warp route for My = 512 when the E-W index is kept (Mx < 2nx - 1, at most 4 row pairs):
+// one warp per row pair, no CTA barrier inside the transform. The pair is transformed
+// forward on the conjugate, Zc = DFT(P_a - i P_b), so Z = conj Zc, split N = 16 x 32 as in
+// the 512-beam kernel (n = n2 + 16 n1, k = k1 + 32 k2): pass 1, lane (n2, h), is the
+// 16-point DFT of (x[n1] + (-1)^h x[n1 + 16]) W32^(h n1), i.e. the outputs k1 = 2m + h of
+// the 32-point DFT over n1, times W512^(n2 k1), stored transposed (row stride 17); pass 2,
+// lane k1, is the 16-point DFT over n2. Zc goes to the warp's region and the two rows
+// separate from Zc[k] and Zc[512 - k]:
+//   X_a[k] = (conj Zc[k] + Zc[N-k]) / 2,   X_b[k] = (conj Zc[k] - Zc[N-k]) / 2i.
+// A CTA of 8 warps takes 8 / pairs (window, channel) tiles per step; the tiles of the next
+// step are fetched with cp.async meanwhile.
+namespace vw {
+constexpr int N = 512, NW = 8, REG = 32 * 17;
+}
+
+__global__ void __launch_bounds__(vw::NW * 32, 2)
+stacked_vis_warp_kernel(const float* __restrict__ P, float2* __restrict__ out,
+                        const float2* __restrict__ tw_y, int64_t nitems, int ny, int mx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int N = vw::N;
+  const int np = (mx + 1) >> 1;                    // row pairs per tile (1, 2 or 4)
+  const int G = vw::NW / np;                       // tiles per step
+  const int tsz = mx * N;                          // floats per tile
+  const int dy_n = 2 * ny - 1;
+  float* tiles = reinterpret_cast<float*>(smem);   // [2][G][Mx * N]
+  float2* tw512 = reinterpret_cast<float2*>(tiles + 2 * G * tsz);   // [32 k1][16 n2] W512^(n2 k1)
+  float2* tw32 = tw512 + 512;                      // [2 h][16 n1] W32^(h n1)
+  float2* regs = tw32 + 32;                        // [NW][REG]
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) tw512[i] = tw_y[(i & 15) * (i >> 4)];
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) tw32[i] = tw_y[16 * (i >> 4) * (i & 15)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = warp / np, pair = warp - slot * np;
+  float2* rg = regs + warp * vw::REG;
+  const float inv = 1.0f / (float)N;
+  const int64_t ngroups = (nitems + G - 1) / G;
+  // tiles g*G .. g*G + G - 1 (those < nitems), 16-byte copies (the tiles are 2 KB multiples)
+  auto fetch = [&](int64_t g, float* dst) {
+    if (g >= ngroups) return;
+    const int64_t i0 = g * G;
+    const int ntile = (int)(nitems - i0 < G ? nitems - i0 : G);
+    const float* src = P + i0 * (int64_t)tsz;
+    for (int i = threadIdx.x; i < (ntile * tsz) >> 2; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+  };
+  int cur = 0;
+  fetch(blockIdx.x, tiles);
+  cp_async_commit();
+  for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    __syncthreads();                               // the other buffer is free again
+    fetch(g + gridDim.x, tiles + (cur ^ 1) * G * tsz);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();                               // this step's tiles are in shared memory
+    const int64_t item = g * G + slot;
+    if (item < nitems) {
+      const float* ra = tiles + cur * G * tsz + slot * tsz + 2 * pair * N;
+      const bool two = 2 * pair + 1 < mx;
+      // ---- pass 1: lane (n2, h)
+      const int n2 = lane & 15, h = lane >> 4;
+      const float sg = h ? -1.f : 1.f;
+      float2 x[16];
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) {
+        const int i0 = n2 + 16 * n1, i1 = i0 + 256;
+        const float2 u = make_float2(ra[i0], two ? -ra[N + i0] : 0.f);
+        const float2 v = make_float2(ra[i1], two ? -ra[N + i1] : 0.f);
+        x[n1] = cmul(make_float2(fmaf(sg, v.x, u.x), fmaf(sg, v.y, u.y)), tw32[h * 16 + n1]);
+      }
+      Dft<16>::run(x);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k1 = 2 * m + h;
+        rg[k1 * 17 + n2] = cmul(x[m], tw512[k1 * 16 + n2]);
+      }
+      __syncwarp();
+      // ---- pass 2: lane k1; Zc[k1 + 32 k2] back into the region
+      float2 y[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) y[q] = rg[lane * 17 + q];
+      Dft<16>::run(y);
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) rg[lane + 32 * k2] = y[k2];
+      __syncwarp();
+      // ---- separate the rows, lags -(ny-1) .. ny-1
+      float2* da = out + item * (int64_t)(mx * dy_n) + (2 * pair) * dy_n;
+      for (int d = lane; d < dy_n; d += 32) {
+        const int lag = d - (ny - 1), k = lag < 0 ? -lag : lag;
+        const float2 zk = rg[k], zm = rg[(N - k) & (N - 1)];
+        float2 xa = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zm.y - zk.y));
+        if (lag < 0) xa.y = -xa.y;
+        da[d] = make_float2(xa.x * inv, xa.y * inv);
+        if (two) {
+          float2 xb = make_float2(-0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+          if (lag < 0) xb.y = -xb.y;
+          da[dy_n + d] = make_float2(xb.x * inv, xb.y * inv);
+        }
+      }
+    }
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+static size_t vis_warp_smem(int mx) {
+  const int np = (mx + 1) >> 1, G = vw::NW / np;
+  return sizeof(float) * 2 * (size_t)G * mx * vw::N + sizeof(float2) * (512 + 32 + (size_t)vw::NW * vw::REG);
+}
+
 }  // namespace fftbf
 
 using namespace fftbf;
@@ -248,6 +357,11 @@ int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_
   const size_t smem = sizeof(float) * (((size_t)p->mx * p->my + 1) & ~(size_t)1) +
                       sizeof(float2) * ((size_t)p->my + p->mx + (size_t)p->mx * dy);
   const bool use_fft = fft && smem_fft <= 200 * 1024;
+  // warp route: 512 N-S beams, E-W index kept, 1, 2 or 4 row pairs, 16-byte aligned beams
+  const int np = (p->mx + 1) / 2;
+  const bool use_warp = inv_y && !inv_x && p->my == 512 && (np == 1 || np == 2 || np == 4) &&
+                        (reinterpret_cast<uintptr_t>(beams_dev) & 15) == 0 &&
+                        vis_warp_smem(p->mx) <= 200 * 1024;
   if (!use_fft && smem > 200 * 1024)
     return set_error(FFTBF_EUNSUPPORTED, "beam tile too large for the stacking kernel");
   int prev = 0;
@@ -256,7 +370,22 @@ int fftbf_stacked_visibilities(fftbf_plan* p, const float* beams_dev, int64_t n_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t items = n_windows * p->nfreq;
   cudaError_t e;
-  if (use_fft) {
+  if (use_warp) {
+    const size_t sm = vis_warp_smem(p->mx);
+    e = cudaFuncSetAttribute(stacked_vis_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stacked_vis_warp_kernel, vw::NW * 32, sm);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    const int64_t groups = (items + vw::NW / np - 1) / (vw::NW / np);
+    const int64_t cap = (int64_t)p->nsm * per_sm;
+    const int64_t grid = groups < cap ? groups : cap;
+    if (e == cudaSuccess) {
+      stacked_vis_warp_kernel<<<(unsigned)grid, vw::NW * 32, sm, st>>>(
+          beams_dev, reinterpret_cast<float2*>(vis_dev), p->d_tw, items, p->ny, p->mx);
+      e = cudaGetLastError();
+    }
+  } else if (use_fft) {
     e = cudaFuncSetAttribute(stacked_vis_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_fft);
     // resident CTAs per SM from shared memory (256 threads each, at most 8 by threads)

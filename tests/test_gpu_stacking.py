@@ -22,7 +22,10 @@ def _lib():
                                    (4, 256, 4, 512, 2, 2, 384, 384),  # E-W kept, N-S lags
                                    (2, 16, 2, 32, 1, 8, 64, 16),      # the tiny workload
                                    (3, 40, 3, 128, 2, 2, 32, 16),     # odd E-W rows: a row paired with zeros
-                                   (2, 10, 3, 24, 1, 2, 16, 8)])      # N-S pad not a power of two: direct route
+                                   (2, 10, 3, 24, 1, 2, 16, 8),       # N-S pad not a power of two: direct route
+                                   (3, 256, 3, 512, 2, 3, 64, 32),    # warp route: two row pairs, one row alone
+                                   (1, 200, 1, 512, 1, 3, 48, 16),    # warp route: one row, 8 tiles per step
+                                   (8, 64, 8, 512, 1, 2, 16, 8)])     # warp route: four row pairs
 def test_stacked_visibilities_match_oracle(shape):
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v8, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="random", seed=90)
