@@ -29,19 +29,28 @@ constexpr int kLocWarps = 8;
 
 struct LocAxis {
   int n, M, fit;
+  int pow2;                           // M is a power of two: residues by masks
   float invM, newton;                 // newton = n^2 / (4 pi^2 MOI)
 };
+
+// k mod M in [0, M)
+__device__ __forceinline__ int mod_m(const LocAxis& ax, int k) {
+  if (ax.pow2) return k & (ax.M - 1);
+  const int r = k % ax.M;
+  return r < 0 ? r + ax.M : r;
+}
 
 // Dirichlet regridding weight of FFT beam B at the position (ih, fr), and its y-derivative.
 __device__ __forceinline__ void dir_weight(const LocAxis& ax, int ih, float fr, int B, float* w,
                                            float* dw) {
   const int M = ax.M, L = 2 * ax.n - 1;
-  int d = (ih - B) % M;                               // e M = d + fr, reduced to [-M/2, M/2)
+  int d = mod_m(ax, ih - B);                          // e M = d + fr, reduced to [-M/2, M/2)
   if ((float)d + fr >= 0.5f * M) d -= M;
-  else if ((float)d + fr < -0.5f * M) d += M;
   const float r = (float)d + fr;
   const float e = r * ax.invM;
-  const int m2 = (int)(((long long)L * d) % (2LL * M));
+  // (2n - 1) d mod 2M, any representative: |L d| <= M^2 / 2 + M fits 32 bits for M <= 32768
+  const int m2 = ax.pow2 ? ((L * d) & (2 * M - 1))
+                         : (M <= 32768 ? (L * d) % (2 * M) : (int)(((long long)L * d) % (2LL * M)));
   float ph = ((float)m2 + (float)L * fr) * ax.invM;   // (2n - 1) e  (mod 2)
   ph -= 2.f * rintf(0.5f * ph);
   float sL, cL, s1, c1;
@@ -62,10 +71,8 @@ __device__ __forceinline__ void dir_weight(const LocAxis& ax, int ih, float fr, 
 }
 
 // first of the k taps nearest y M = ih + fr: floor(y M - (k - 1)/2 + 1/2), mod M
-__device__ __forceinline__ int first_tap(int M, int ih, float fr, int k) {
-  int f = ih + (int)floorf(fr + 0.5f - 0.5f * (float)(k - 1));
-  f %= M;
-  return f < 0 ? f + M : f;
+__device__ __forceinline__ int first_tap(const LocAxis& ax, int ih, float fr, int k) {
+  return mod_m(ax, ih + (int)floorf(fr + 0.5f - 0.5f * (float)(k - 1)));
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -80,13 +87,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // advance a position by dy (in units of y) and renormalise fr into [0, 1), ih into [0, M)
-__device__ __forceinline__ void move(int M, int* ih, float* fr, float dyM) {
+__device__ __forceinline__ void move(const LocAxis& ax, int* ih, float* fr, float dyM) {
   float f = *fr + dyM;
   const float k = floorf(f);
   f -= k;
   if (f >= 1.f) f = 0.f;                               // rounding of f - k at the top end
-  int i = (*ih + (int)k) % M;
-  *ih = i < 0 ? i + M : i;
+  *ih = mod_m(ax, *ih + (int)k);
   *fr = f;
 }
 
@@ -132,36 +138,41 @@ __global__ void __launch_bounds__(32 * kLocWarps, 4) localise_kernel(
     int ihx = a0, ihy = b0;
     float frx = 0.f, fry = 0.f;
     const int kx = axx.fit ? taps_x : 1, ky = axy.fit ? taps_y : 1;
+    // this lane's first tap pair (tx, ty) of the k_x k_y products, and the step for q += 32
+    const int tx0 = lane / ky, ty0 = lane - tx0 * ky;
+    const int stx = 32 / ky, sty = 32 - stx * ky;
     for (int it = 0; it < n_iter; ++it) {
-      const int fx = axx.fit ? first_tap(mx, ihx, frx, kx) : a0;
-      const int fy = axy.fit ? first_tap(my, ihy, fry, ky) : b0;
+      const int fx = axx.fit ? first_tap(axx, ihx, frx, kx) : a0;
+      const int fy = axy.fit ? first_tap(axy, ihy, fry, ky) : b0;
       for (int t = lane; t < kx; t += 32) {
         float w = 1.f, d = 0.f;
-        if (axx.fit) dir_weight(axx, ihx, frx, (fx + t) % mx, &w, &d);
+        if (axx.fit) dir_weight(axx, ihx, frx, mod_m(axx, fx + t), &w, &d);
         wx[t] = w;
         dwx[t] = d;
       }
       for (int t = lane; t < ky; t += 32) {
         float w = 1.f, d = 0.f;
-        if (axy.fit) dir_weight(axy, ihy, fry, (fy + t) % my, &w, &d);
+        if (axy.fit) dir_weight(axy, ihy, fry, mod_m(axy, fy + t), &w, &d);
         wy[t] = w;
         dwy[t] = d;
       }
       __syncwarp();
       float T = 0.f, Dx = 0.f, Dy = 0.f;
-      for (int q = lane; q < kx * ky; q += 32) {
-        const int tx = q / ky, ty = q - (q / ky) * ky;
-        const float p = tile[((fx + tx) % mx) * my + (fy + ty) % my];
+      for (int q = lane, tx = tx0, ty = ty0; q < kx * ky; q += 32) {
+        const float p = tile[mod_m(axx, fx + tx) * my + mod_m(axy, fy + ty)];
         T = fmaf(wx[tx] * wy[ty], p, T);
         Dx = fmaf(dwx[tx] * wy[ty], p, Dx);
         Dy = fmaf(wx[tx] * dwy[ty], p, Dy);
+        tx += stx;                                       // q += 32
+        ty += sty;
+        if (ty >= ky) { ty -= ky; ++tx; }
       }
       T = warp_sum_f(T);
       Dx = warp_sum_f(Dx);
       Dy = warp_sum_f(Dy);
       __syncwarp();
-      if (axx.fit) move(mx, &ihx, &frx, Dx * axx.newton / T * (float)mx);
-      if (axy.fit) move(my, &ihy, &fry, Dy * axy.newton / T * (float)my);
+      if (axx.fit) move(axx, &ihx, &frx, Dx * axx.newton / T * (float)mx);
+      if (axy.fit) move(axy, &ihy, &fry, Dy * axy.newton / T * (float)my);
     }
     // the pointed beam at the estimate, from every FFT beam: sum_B w^B sum_A w^A P[A, B]
     double T = 0.0;
@@ -219,6 +230,7 @@ extern "C" int fftbf_localise(fftbf_plan* p, const float* beams_dev, int64_t n_w
     a.n = n;
     a.M = M;
     a.fit = M >= 2 * n - 1 && n > 1;
+    a.pow2 = (M & (M - 1)) == 0;
     a.invM = (float)(1.0 / M);
     double moi = 0.0;
     for (int d = -(n - 1); d < n; ++d) moi += (double)d * d * (n - (d < 0 ? -d : d));
