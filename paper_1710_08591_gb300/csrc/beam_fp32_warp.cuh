@@ -69,6 +69,22 @@ template <int MX, int R> struct WarpCfg {
   static constexpr int H = 32 / D;                      // k1 classes per n2
 };
 
+// Physical row of tile row x (x < 32) in a transform region of rows of R complex values:
+// for R <= 8 a warp's stores cover 32 / R consecutive rows (E-W stage: input rows n1;
+// pass 1: rows k1 = H m + h of one m), which the row stride R + 1 would put in shared
+// banks; x / (32 / R) + R (x mod 32 / R) spreads them so that every bank takes two words.
+// Pass 2 then reads physical row `lane`, which holds k1 = prow_inv(lane).
+template <int R>
+__device__ __forceinline__ int prow(int x) {
+  if constexpr (R <= 8) return x / (32 / R) + R * (x % (32 / R));
+  else return x;
+}
+template <int R>
+__device__ __forceinline__ int prow_inv(int y) {
+  if constexpr (R <= 8) return (32 / R) * (y % R) + y / R;
+  else return y;
+}
+
 // FULL: the lattice is MX x NH feeds, all live, with an MX-point E-W DFT (the radix-3
 // butterfly for MX = 3) and 16-byte aligned voltages, i.e. exactly 2x N-S padding: its
 // sizes are compile-time constants.
@@ -134,7 +150,7 @@ __device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* 
         }
       }
     }
-    const int slot = (iy % R) + stride * (iy / R);
+    const int slot = (iy % R) + stride * prow<R>(iy / R);
 #pragma unroll
     for (int A = 0; A < MX; ++A) regs[(s * MX + A) * reg + slot] = z[A];
   }
@@ -203,13 +219,13 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
         for (int q = 0; q < D; ++q) y[q] = czero();
 #pragma unroll
         for (int n1 = 0; n1 < 16; ++n1)
-          y[n1 % D] = cadd(y[n1 % D], cmul(rg[n2 + (R + 1) * n1], w32[(n1 * h) & 31]));
+          y[n1 % D] = cadd(y[n1 % D], cmul(rg[n2 + (R + 1) * prow<R>(n1)], w32[(n1 * h) & 31]));
         Dft<D>::run(y);
         __syncwarp();
 #pragma unroll
         for (int m = 0; m < D; ++m) {
           const int k1 = H * m + h;
-          rg[k1 * (R + 1) + n2] = cmul(y[m], twk[k1 * R + n2]);
+          rg[prow<R>(k1) * (R + 1) + n2] = cmul(y[m], twk[k1 * R + n2]);
         }
       } else {
         const int n2 = lane;
@@ -244,9 +260,10 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
   }
   // ---- window complete: add the S snapshot slots of each E-W beam in order, write once
   float* dst = a.beams + item * (int64_t)(MX * N);
+  const int k1o = prow_inv<R>(lane);              // the k1 this lane's pass 2 produced
   if constexpr (S == 1 && J == 1) {
 #pragma unroll
-    for (int k2 = 0; k2 < R; ++k2) dst[warp * N + lane + 32 * k2] = acc[0][k2];
+    for (int k2 = 0; k2 < R; ++k2) dst[warp * N + k1o + 32 * k2] = acc[0][k2];
     __syncthreads();
   } else {
     __syncthreads();
@@ -254,7 +271,7 @@ __device__ __forceinline__ void warp_item(const BeamArgs& a, int64_t item, unsig
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < R; ++k2) red[(warp + wt::kWarps * j) * N + lane + 32 * k2] = acc[j][k2];
+      for (int k2 = 0; k2 < R; ++k2) red[(warp + wt::kWarps * j) * N + k1o + 32 * k2] = acc[j][k2];
     __syncthreads();
     for (int o = threadIdx.x; o < MX * N; o += kThreads) {
       const int A = o / N, k = o - A * N;
