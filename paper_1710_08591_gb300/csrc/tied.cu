@@ -230,32 +230,39 @@ __global__ void tied_compact_table_kernel(int nx, int ny, int mx, int my, int mo
   }
 }
 
-// out[j,f,s] = sum_{tx<kx, ty<ky} cx[tx] cy[ty] P[j,f,(fx+tx) mod Mx,(fy+ty) mod My]: one
-// thread per (window, channel, pointing), pointings fastest so a CTA shares P[j,f].
+// out[j,f,s] = sum_{tx<kx, ty<ky} cx[tx] cy[ty] P[j,f,(fx+tx) mod Mx,(fy+ty) mod My]: a
+// thread per (channel, pointing), pointings fastest, looping over windows (grid z), so the
+// pointing's taps and weights are fetched once and no index needs a division.
 __global__ void __launch_bounds__(256) tied_compact_kernel(const float* __restrict__ P,
                                                             const int* __restrict__ first,
                                                             const float* __restrict__ cw,
                                                             float* __restrict__ out, int64_t nwin,
                                                             int nfreq, int n_tied, int mx,
                                                             int my, int kx, int ky) {
-  const int64_t total = nwin * nfreq * (int64_t)n_tied;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t jf = i / n_tied;
-    const int s = (int)(i - jf * n_tied);
-    const int f = (int)(jf % nfreq);
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_tied) return;
+  for (int f = blockIdx.y; f < nfreq; f += gridDim.y) {
     const int64_t fs = (int64_t)f * n_tied + s;
-    const float* Pj = P + jf * (int64_t)(mx * my);
     const float* c = cw + fs * (kx + ky);
     const int fx = first[2 * fs], fy = first[2 * fs + 1];
-    float acc = 0.f;
-    for (int tx = 0; tx < kx; ++tx) {
-      const float* row = Pj + ((fx + tx) % mx) * my;
-      float racc = 0.f;
-      for (int ty = 0; ty < ky; ++ty) racc = fmaf(c[kx + ty], __ldg(row + (fy + ty) % my), racc);
-      acc = fmaf(c[tx], racc, acc);
+    for (int64_t j = blockIdx.z; j < nwin; j += gridDim.z) {
+      const int64_t jf = j * nfreq + f;
+      const float* Pj = P + jf * (int64_t)(mx * my);
+      float acc = 0.f;
+      int rx = fx;                                    // (fx + tx) mod Mx, fx < Mx, kx <= Mx
+      for (int tx = 0; tx < kx; ++tx) {
+        const float* row = Pj + rx * my;
+        float racc = 0.f;
+        int cy = fy;                                  // (fy + ty) mod My
+        for (int ty = 0; ty < ky; ++ty) {
+          racc = fmaf(c[kx + ty], __ldg(row + cy), racc);
+          if (++cy == my) cy = 0;
+        }
+        acc = fmaf(c[tx], racc, acc);
+        if (++rx == mx) rx = 0;
+      }
+      out[jf * n_tied + s] = acc;
     }
-    out[i] = acc;
   }
 }
 
@@ -617,10 +624,10 @@ int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfre
                 int my, float* out, cudaStream_t st) {
   if (nwin <= 0) return FFTBF_OK;
   if (tt.kx > 0 && tt.ky > 0) {
-    const int64_t total = nwin * nfreq * (int64_t)tt.n_tied;
-    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20);
-    tied_compact_kernel<<<blocks, 256, 0, st>>>(beams, tt.first, tt.cw, out, nwin, nfreq,
-                                                tt.n_tied, mx, my, tt.kx, tt.ky);
+    dim3 grid((tt.n_tied + 255) / 256, (unsigned)std::min(nfreq, 65535),
+              (unsigned)std::min<int64_t>(nwin, 16));
+    tied_compact_kernel<<<grid, 256, 0, st>>>(beams, tt.first, tt.cw, out, nwin, nfreq,
+                                              tt.n_tied, mx, my, tt.kx, tt.ky);
     FFTBF_CUDA_TRY(cudaGetLastError());
     return FFTBF_OK;
   }
