@@ -366,6 +366,21 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize(dev)
             fms = f0.elapsed_time(f1) / fsteps
             forms[form] = {"value": samples_per_step() * world / (fms / 1e3), "ms_per_step": fms}
+            # the beam kernel of the form: the step less the FP32 step's tied-beam share, per
+            # launch, against the tensor roof as specified (512 flops per antenna-sample as
+            # real-embedded GEMMs, 3x for the split form) and against HBM (1.0104 B per sample)
+            tied_ms = max(0.0, ms_step - ncall * (sum(kern_ms) / len(kern_ms)))
+            b_ms = (fms - tied_ms) / ncall
+            sl = T_DEV * nfreq * npol * nx * ny
+            tf = (1536.0 if form == "tc_fp16x3" else 512.0) * sl / (b_ms / 1e3) / 1e12
+            gb = 1.0104 * sl / (b_ms / 1e3) / 1e9
+            pk, psrc = measured_peaks()
+            forms[form]["roofline"] = {
+                "kernel": "beams_tc_kernel", "ms_per_launch": b_ms,
+                "tensor": {"achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                           "frac": tf / pk["bf16_tflops"], "peak_source": psrc + " bf16 burst (fp16 the same rate)"},
+                "hbm": {"achieved": gb, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": gb / pk["hbm_gbs"], "peak_source": psrc}}
             fplan.close()
 
     # ---- tied-beam variants on the step's 128 windows: plain (Dirichlet, GEMM over the 512
