@@ -637,6 +637,24 @@ def run_profile_case(args):
     block = synth.volts(T, nfreq, npol, nx, ny, seed=WL["seed"], sigma=WL["sigma"], sources=src)
     w = synth.separable_weights(synth.half_sine(nx), synth.half_sine(ny))
     u, v = synth.tied_pointings(WL["seed"] + 1, nfreq, n_tied, nx, ny, mx, my)
+    if args.products:
+        # the intensity-space products on 40 windows x 1024 channels of positive synthetic
+        # beams (335 MB, above L2): stacked visibilities and localisation, twice each
+        nw, nf = 40, 1024
+        g = torch.Generator(device="cuda")
+        g.manual_seed(WL["seed"] + 7)
+        pb = torch.rand((nw, nf, mx, my), device="cuda", generator=g) + 1.0
+        with fb.plan_create(nx, ny, mx, my, npol, nf, n_int, weights=w) as plan:
+            dx, dy = fb.stacked_shape(plan)
+            vis = torch.empty((nw, nf, dx, dy), dtype=torch.complex64, device="cuda")
+            loc = torch.empty((nw, nf, 3), device="cuda")
+            for _ in range(2):
+                fb.stacked_visibilities(plan, pb, nw, vis)
+            for _ in range(2):
+                fb.localise(plan, pb, nw, loc, 5, 10)
+            fb.plan_sync(plan)
+        print("profile case (products) done")
+        return 0
     dvol = torch.from_numpy(block.reshape(-1)).cuda()
     beams = torch.empty((T // n_int, nfreq, mx, my), device="cuda")
     tied = torch.empty((T // n_int, nfreq, n_tied), device="cuda")
@@ -667,6 +685,8 @@ def main():
     ap.add_argument("--serve-frames", type=int, default=6000)
     ap.add_argument("--profile-case", action="store_true",
                     help="run a small case of the timed kernels (for ncu) and exit")
+    ap.add_argument("--products", action="store_true",
+                    help="with --profile-case: the stacked-visibility and localisation kernels")
     args = ap.parse_args()
     if args.profile_case and args.workload == "batched":
         return run_batched(args)
