@@ -275,7 +275,11 @@ constexpr int TS = 64, TJ = 64, TK = 16;
 // The K loop runs over the E-W beams A that some pointing of the tile weights (one or two
 // for a one-hot E-W axis, the pointings being sorted by it) and the N-S beams B:
 //   out[j, f, perm(s)] = sum_A sum_B wx[f, s, A] wy[f, s, B] P[j, f, A, B].
-constexpr int GM = 128, GN = 128, GK = 16;
+#ifndef FFTBF_TIED_GK
+#define FFTBF_TIED_GK 16          // FFT beams per K step of the GEMM (8 or 16)
+#endif
+constexpr int GM = 128, GN = 128, GK = FFTBF_TIED_GK;
+constexpr int GEPT = GK / 2;      // staged elements per thread and operand per K step
 #ifndef FFTBF_TIED_MIN_BLOCKS
 #define FFTBF_TIED_MIN_BLOCKS 2   // CTAs per SM the register budget of the GEMM targets
 #endif
@@ -306,21 +310,21 @@ __global__ void __launch_bounds__(256, FFTBF_TIED_MIN_BLOCKS) tied_gemm128_kerne
   __syncthreads();
   const unsigned long long active = s_active;
   const int kb = (my + GK - 1) / GK;
-  // load mapping: row (pointing / window) = tid >> 1, eight consecutive k from (tid & 1) * 8
-  // (two float4 when the rows are 16-byte aligned)
-  const int lr = tid >> 1, lk = (tid & 1) * 8;
+  // load mapping: row (pointing / window) = tid >> 1, GK / 2 consecutive k from
+  // (tid & 1) * GK / 2 (float4 loads when the rows are 16-byte aligned)
+  const int lr = tid >> 1, lk = (tid & 1) * GEPT;
   const int gs = s0 + lr;
   const int64_t gj = j0 + lr;
   const bool vec = (my & 3) == 0;
-  float ra[8], rb[8];
+  float ra[GEPT], rb[GEPT];
   auto load = [&](int A, int b0) {
     const float w = gs < n_tied ? wx[(fs0 + gs) * mx + A] : 0.f;
     const float* wrow = wy + (fs0 + gs) * my + b0 + lk;
     const float* prow_p = P + gj * prow + (int64_t)f * mx * my + (int64_t)A * my + b0 + lk;
     const bool rin = gs < n_tied, pin = gj < nwin;
-    if (vec && b0 + lk + 8 <= my) {
+    if (vec && b0 + lk + GEPT <= my) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < GEPT / 4; ++h) {
         const float4 a = rin ? *reinterpret_cast<const float4*>(wrow + 4 * h) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 p = pin ? *reinterpret_cast<const float4*>(prow_p + 4 * h) : make_float4(0.f, 0.f, 0.f, 0.f);
         ra[4 * h] = w * a.x; ra[4 * h + 1] = w * a.y; ra[4 * h + 2] = w * a.z; ra[4 * h + 3] = w * a.w;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(256, FFTBF_TIED_MIN_BLOCKS) tied_gemm128_kerne
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < GEPT; ++i) {
         const bool kin = b0 + lk + i < my;
         ra[i] = (rin && kin) ? w * wrow[i] : 0.f;
         rb[i] = (pin && kin) ? prow_p[i] : 0.f;
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(256, FFTBF_TIED_MIN_BLOCKS) tied_gemm128_kerne
   };
   auto store = [&](int buf) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < GEPT; ++i) {
       As[buf][lk + i][lr] = ra[i];
       Bs[buf][lk + i][lr] = rb[i];
     }
