@@ -226,6 +226,7 @@ int fftbf_tied_beams(fftbf_plan* p, const float* beams, int64_t n_windows, int n
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = tied_prepare(p->tied, p->nx, p->ny, p->mx, p->my, p->nfreq, n_tied, u, v, st);
   if (rc != FFTBF_OK) return rc;
+  p->tied.err = p->d_err;
   rc = tied_launch(p->tied, beams, n_windows, p->nfreq, p->mx, p->my, tied, st);
   if (rc == FFTBF_OK) remember_stream(p, st);
   return rc;

@@ -121,10 +121,26 @@ struct TiedTables {
   int* perm = nullptr;          // [nfreq][n_tied] sorted slot -> caller's pointing index
   double* duv = nullptr;        // device scratch for u, v
   size_t cap_tied = 0;
+  // tensor-core path (E-W axis on the grid): split FP16 weight rows and their exponents,
+  // the E-W beam of each sorted pointing, and per-call split beam rows
+  int tc = 0;
+  uint16_t* wyh = nullptr;      // [nfreq][n_tied][my] FP16 hi of 2^e wx wy
+  uint16_t* wyl = nullptr;      // [nfreq][n_tied][my] FP16 lo
+  int* wye = nullptr;           // [nfreq][n_tied] row exponent e
+  int* wa = nullptr;            // [nfreq][n_tied] E-W beam of the pointing
+  uint16_t* ph = nullptr;       // [nwin][nfreq][mx][my] FP16 hi of the beams (scratch)
+  uint16_t* pl = nullptr;
+  int* pe = nullptr;            // [nwin][nfreq][mx] beam row exponents
+  size_t p_cap = 0;             // rows of ph / pl / pe
+  int* err = nullptr;           // the plan's device error word (bounded waits)
 };
+bool tied_tc_eligible(bool dense_x, int mx, int my);
+int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st);
+int tied_tc_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx, int my,
+                   float* out, cudaStream_t st);
 int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int n_tied,
                  const double* u, const double* v, cudaStream_t st);
-int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
+int tied_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
                 int my, float* out, cudaStream_t st);
 void tied_free(TiedTables& tt);
 

@@ -474,6 +474,13 @@ __global__ void __launch_bounds__(256) tied_gemm_kernel(const float* __restrict_
 }
 
 void tied_free(TiedTables& tt) {
+  cudaFree(tt.wyh);
+  cudaFree(tt.wyl);
+  cudaFree(tt.wye);
+  cudaFree(tt.wa);
+  cudaFree(tt.ph);
+  cudaFree(tt.pl);
+  cudaFree(tt.pe);
   cudaFree(tt.wx);
   cudaFree(tt.wy);
   cudaFree(tt.perm);
@@ -549,6 +556,7 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
   tt.perm = tt.first = nullptr;
   tt.duv = tt.d_g = nullptr;
   tt.cap_tied = 0;
+  tt.tc = 0;
   const size_t ng = tt.win_x.g.size() + tt.win_y.g.size();
   bool ok = cudaMalloc(&tt.perm, nuv * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&tt.duv, 2 * nuv * sizeof(double)) == cudaSuccess &&
@@ -618,15 +626,21 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
     int rc = axis_table(nx, mx, mode_x, gx, tt.win_x.trunc, tt.duv, tt.wx);
     if (rc == FFTBF_OK) rc = axis_table(ny, my, mode_y, gy, tt.win_y.trunc, tt.duv + nuv, tt.wy);
     if (rc != FFTBF_OK) return rc;
+    tt.tc = 0;
+    if (tied_tc_eligible(dense_x, mx, my)) {
+      rc = tied_tc_build(tt, (int64_t)nuv, mx, my, st);
+      if (rc != FFTBF_OK) return rc;
+    }
   }
   tt.built_version = tt.version;
   tt.n_tied = n_tied;
   return FFTBF_OK;
 }
 
-int tied_launch(const TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
+int tied_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx,
                 int my, float* out, cudaStream_t st) {
   if (nwin <= 0) return FFTBF_OK;
+  if (tt.tc && tt.kx == 0) return tied_tc_launch(tt, beams, nwin, nfreq, mx, my, out, st);
   if (tt.kx > 0 && tt.ky > 0) {
     dim3 grid((tt.n_tied + 255) / 256, (unsigned)std::min(nfreq, 65535),
               (unsigned)std::min<int64_t>(nwin, 16));

@@ -1,0 +1,319 @@
+// Tied-array beams on the tensor cores (Eq. bp_max_arbitrary as a GEMM) when the E-W axis
+// is on the FFT-beam grid (pad_x < 2 nx - 1, at most 4 E-W beams): per channel f,
+//   out[j, s] = sum_B wx[s, A_s] wy[s, B] P[j, f, A_s, B],
+// a [pointings x beams] x [beams x windows] product for each E-W beam A. Operands are
+// split FP16 pairs, x = 2^-e (hi + lo) with hi = fp16(2^e x), lo = fp16(2^e x - hi), and
+// each K step accumulates hi*hi + hi*lo + lo*hi in FP32 (tcgen05.mma kind::f16, TMEM), which
+// keeps FP32 accuracy; e scales every weight row and every beam row so that its largest
+// magnitude lies in [2^14, 2^15) (inside the FP16 range, with the residuals normal), and the
+// epilogue divides by 2^(e_s + e_j) exactly. A CTA computes 128 pointings x 128 windows of
+// one channel: K chunks of 64 beams are staged by cp.async (three buffers, two chunks ahead
+// of the MMAs; zero rows past the ends), one TMEM accumulator of 128 columns per E-W
+// beam used by the tile's pointings, and each pointing (TMEM lane) reads its own beam's
+// accumulator. Waits on MMA completion are bounded; a timeout sets the plan's error word.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "beam_fp32.cuh"
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace fftbf {
+
+namespace ttc {
+constexpr int TM = 128, TN = 128, KC = 64;     // pointings, windows, beams per K chunk
+constexpr int LBO = 128, SBO = 1024;           // canonical K-major tile: 8 K blocks per row group
+constexpr int TILE = TM * KC * 2;              // bytes of one 128 x 64 FP16 tile
+constexpr int STAGE = 4 * TILE;                // W hi, W lo, P hi, P lo
+constexpr int NT = 128;
+constexpr int NS = 3;                          // staging buffers
+constexpr int MAXA = 4;                        // E-W beams (one accumulator each)
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t WAIT_NS = 1000000000ull;
+}  // namespace ttc
+
+// 16-byte cp.async that writes zeros instead of reading when !valid
+__device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+
+// e such that 2^e m lies in [2^14, 2^15) (0 for a zero row)
+__device__ __forceinline__ int split_exp(float m) { return m > 0.f ? 14 - ilogbf(m) : 0; }
+
+// Split rows of x (one warp per row): hi, lo and the row exponent.
+__device__ __forceinline__ void split_row(const float* x, float scale_in, int n, __half* hi,
+                                          __half* lo, int* e_out, int lane) {
+  float m = 0.f;
+  for (int b = lane; b < n; b += 32) m = fmaxf(m, fabsf(scale_in * x[b]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = split_exp(m);
+  for (int b = lane; b < n; b += 32) {
+    const float v = ldexpf(scale_in * x[b], e);
+    const __half h = __float2half_rn(v);
+    hi[b] = h;
+    lo[b] = __float2half_rn(v - __half2float(h));
+  }
+  if (lane == 0) *e_out = e;
+}
+
+// Weight tables (sorted pointing order): the row's E-W beam A_s (the largest |wx|) and the
+// split of wx[s, A_s] wy[s, :].
+__global__ void tied_tc_table_kernel(const float* __restrict__ wx, const float* __restrict__ wy,
+                                     int64_t nrows, int mx, int my, __half* wyh, __half* wyl,
+                                     int* wye, int* wa) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nw) {
+    int A = 0;
+    float best = -1.f;
+    for (int a = 0; a < mx; ++a) {
+      const float v = fabsf(wx[r * mx + a]);
+      if (v > best) { best = v; A = a; }
+    }
+    split_row(wy + r * my, wx[r * mx + A], my, wyh + r * my, wyl + r * my, wye + r, lane);
+    if (lane == 0) wa[r] = A;
+  }
+}
+
+// Beam rows P[j, f, A, :] split the same way (per call).
+__global__ void tied_tc_prep_kernel(const float* __restrict__ P, int64_t nrows, int my,
+                                    __half* ph, __half* pl, int* pe) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nw)
+    split_row(P + r * my, 1.f, my, ph + r * my, pl + r * my, pe + r, lane);
+}
+
+__global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
+    const __half* __restrict__ wyh, const __half* __restrict__ wyl, const int* __restrict__ wye,
+    const int* __restrict__ wa, const int* __restrict__ perm, const __half* __restrict__ ph,
+    const __half* __restrict__ pl, const int* __restrict__ pe, float* __restrict__ out,
+    int64_t nwin, int nfreq, int n_tied, int mx, int my, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_t[];
+  __shared__ uint64_t bars[ttc::NS];
+  __shared__ uint32_t taddr;
+  __shared__ int s_mask;
+  __shared__ int s_pe[ttc::MAXA][ttc::TN];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int f = blockIdx.z;
+  const int s0 = blockIdx.x * ttc::TM;
+  const int64_t j0 = (int64_t)blockIdx.y * ttc::TN;
+  const int64_t fs0 = (int64_t)f * n_tied;
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr, ttc::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < ttc::NS; ++i) tc::mbar_init(&bars[i], 1);
+    tc::mbar_init_fence();
+    s_mask = 0;
+  }
+  __syncthreads();
+  const int s = s0 + tid;
+  const bool srow = s < n_tied;
+  const int my_a = srow ? wa[fs0 + s] : 0;
+  const int my_e = srow ? wye[fs0 + s] : 0;
+  if (srow) atomicOr(&s_mask, 1 << my_a);
+  __syncthreads();
+  const int mask = s_mask;
+  int nact = 0, my_ai = 0;
+  for (int A = 0; A < mx; ++A)
+    if ((mask >> A) & 1) {
+      if (A == my_a) my_ai = nact;
+      ++nact;
+    }
+  // exponents of the tile's windows, per E-W beam in use
+  for (int i = tid; i < nact * ttc::TN; i += ttc::NT) {
+    const int ai = i / ttc::TN, jj = i - ai * ttc::TN;
+    int A = 0;
+    for (int a = 0, c = -1; a < mx; ++a)
+      if ((mask >> a) & 1 && ++c == ai) A = a;
+    const int64_t j = j0 + jj;
+    s_pe[ai][jj] = j < nwin ? pe[(j * nfreq + f) * mx + A] : 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = taddr;
+  const int kcs = my / ttc::KC;
+  const int total = nact * kcs;
+  const uint32_t idesc = tc::idesc_f16(ttc::TM, ttc::TN, false);
+  bool ok = true;
+  // chunk t = (E-W beam in use number t / kcs, K chunk t % kcs) is staged in buffer t % NS,
+  // NS - 1 chunks ahead of the MMAs; a buffer is refilled once its MMAs have completed
+  auto chunk_beam = [&](int t) {
+    const int want = t / kcs;
+    int A = 0;
+    for (int a = 0, c = -1; a < mx; ++a)
+      if ((mask >> a) & 1 && ++c == want) A = a;
+    return A;
+  };
+  auto load = [&](int t) {
+    unsigned char* stg = smem_t + (t % ttc::NS) * ttc::STAGE;
+    const int A = chunk_beam(t), kc = t % kcs;
+    for (int idx = tid; idx < 4 * ttc::TM * 8; idx += ttc::NT) {
+      const int tile = idx >> 10, r = (idx >> 3) & 127, kb = idx & 7;
+      unsigned char* dst = stg + tile * ttc::TILE + tc::kmajor_off(r, kb * 8, ttc::LBO, ttc::SBO);
+      const int k0 = kc * ttc::KC + kb * 8;
+      if (tile < 2) {
+        const bool v = s0 + r < n_tied;
+        const __half* src = (tile == 0 ? wyh : wyl) + (v ? (fs0 + s0 + r) * my + k0 : 0);
+        cp_async16_z(dst, src, v);
+      } else {
+        const int64_t j = j0 + r;
+        const bool v = j < nwin;
+        const __half* src = (tile == 2 ? ph : pl) + (v ? ((j * nfreq + f) * mx + A) * my + k0 : 0);
+        cp_async16_z(dst, src, v);
+      }
+    }
+  };
+  for (int t = 0; t < ttc::NS - 1; ++t) {         // prologue: NS - 1 groups (empty past the end)
+    if (t < total) load(t);
+    cp_async_commit();
+  }
+  for (int t = 0; t < total; ++t) {
+    cp_async_wait<ttc::NS - 2>();                 // chunk t has landed
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(smem_t + (t % ttc::NS) * ttc::STAGE);
+      const uint32_t d = tbase + (uint32_t)((t / kcs) * ttc::TN);
+      const int kc = t % kcs;
+#pragma unroll
+      for (int ks = 0; ks < ttc::KC / 16; ++ks) {
+        const uint32_t ko = (uint32_t)(ks * 2 * ttc::LBO);
+        const uint64_t dwh = tc::smem_desc(sa + ko, ttc::LBO, ttc::SBO);
+        const uint64_t dwl = tc::smem_desc(sa + ttc::TILE + ko, ttc::LBO, ttc::SBO);
+        const uint64_t dph = tc::smem_desc(sa + 2 * ttc::TILE + ko, ttc::LBO, ttc::SBO);
+        const uint64_t dpl = tc::smem_desc(sa + 3 * ttc::TILE + ko, ttc::LBO, ttc::SBO);
+        tc::mma_f16(d, dwh, dph, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+        tc::mma_f16(d, dwh, dpl, idesc, 1u);
+        tc::mma_f16(d, dwl, dph, idesc, 1u);
+      }
+      tc::mma_commit(&bars[t % ttc::NS]);
+    }
+    const int tn = t + ttc::NS - 1;               // next chunk to stage, into buffer (t - 1) % NS
+    if (tn < total) {
+      if (t >= 1) {
+        ok = tc::mbar_wait(&bars[(t - 1) % ttc::NS], (uint32_t)(((t - 1) / ttc::NS) & 1), ttc::WAIT_NS);
+        if (!__syncthreads_and(ok)) break;
+      }
+      load(tn);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();                             // no copy left in flight (also on a timeout)
+  // the last commit covers every MMA of the CTA
+  if (ok && total > 0) {
+    const int tl = total - 1;
+    ok = tc::mbar_wait(&bars[tl % ttc::NS], (uint32_t)((tl / ttc::NS) & 1), ttc::WAIT_NS);
+    ok = __syncthreads_and(ok);
+  }
+  tc::fence_after_sync();
+  if (ok && total > 0) {
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const int dst_s = srow ? perm[fs0 + s] : 0;
+    for (int c = 0; c < ttc::TN / 32; ++c) {
+      for (int a2 = 0; a2 < nact; ++a2) {
+        uint32_t r[32];
+        tc::tmem_ld32(tbase + lane_off + (uint32_t)(a2 * ttc::TN + 32 * c), r);
+        tc::tmem_wait_ld();
+        if (a2 == my_ai && srow) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int64_t j = j0 + 32 * c + q;
+            if (j < nwin)
+              out[(j * nfreq + f) * (int64_t)n_tied + dst_s] =
+                  ldexpf(__uint_as_float(r[q]), -(my_e + s_pe[a2][32 * c + q]));
+          }
+        }
+      }
+    }
+  } else if (!ok && tid == 0) {
+    atomicExch(err, FFTBF_ETIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, ttc::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------------------ host --
+bool tied_tc_eligible(bool dense_x, int mx, int my) {
+  const char* env = getenv("FFTBF_TIED_TC");
+  if (env && env[0] == '0') return false;
+  return !dense_x && mx <= ttc::MAXA && my >= ttc::KC && my % ttc::KC == 0;
+}
+
+int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st) {
+  cudaFree(tt.wyh);
+  cudaFree(tt.wyl);
+  cudaFree(tt.wye);
+  cudaFree(tt.wa);
+  tt.wyh = tt.wyl = nullptr;
+  tt.wye = tt.wa = nullptr;
+  bool ok = cudaMalloc(&tt.wyh, nuv * my * sizeof(__half)) == cudaSuccess &&
+            cudaMalloc(&tt.wyl, nuv * my * sizeof(__half)) == cudaSuccess &&
+            cudaMalloc(&tt.wye, nuv * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&tt.wa, nuv * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return set_error(FFTBF_ENOMEM, "cannot allocate the split tied-beam tables");
+  }
+  const unsigned blocks = (unsigned)std::min<int64_t>((nuv + 7) / 8, 1 << 20);
+  tied_tc_table_kernel<<<blocks, 256, 0, st>>>(tt.wx, tt.wy, nuv, mx, my,
+                                               reinterpret_cast<__half*>(tt.wyh),
+                                               reinterpret_cast<__half*>(tt.wyl), tt.wye, tt.wa);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  tt.tc = 1;
+  return FFTBF_OK;
+}
+
+int tied_tc_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx, int my,
+                   float* out, cudaStream_t st) {
+  const int64_t nrows = nwin * nfreq * mx;
+  if ((size_t)nrows > tt.p_cap) {
+    cudaStreamSynchronize(st);                  // the old scratch may still be read
+    cudaFree(tt.ph);
+    cudaFree(tt.pl);
+    cudaFree(tt.pe);
+    tt.ph = tt.pl = nullptr;
+    tt.pe = nullptr;
+    tt.p_cap = 0;
+    bool ok = cudaMalloc(&tt.ph, nrows * my * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&tt.pl, nrows * my * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&tt.pe, nrows * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return set_error(FFTBF_ENOMEM, "cannot allocate the split beam scratch");
+    }
+    tt.p_cap = (size_t)nrows;
+  }
+  const unsigned pblocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 1 << 20);
+  tied_tc_prep_kernel<<<pblocks, 256, 0, st>>>(beams, nrows, my, reinterpret_cast<__half*>(tt.ph),
+                                               reinterpret_cast<__half*>(tt.pl), tt.pe);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  const int64_t jt = (nwin + ttc::TN - 1) / ttc::TN;
+  if (jt > 65535 || nfreq > 65535)
+    return set_error(FFTBF_EUNSUPPORTED, "tied beams: too many windows or channels per call");
+  const size_t smem = ttc::NS * (size_t)ttc::STAGE;
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(tied_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  dim3 grid((tt.n_tied + ttc::TM - 1) / ttc::TM, (unsigned)jt, nfreq);
+  tied_tc_kernel<<<grid, ttc::NT, smem, st>>>(
+      reinterpret_cast<const __half*>(tt.wyh), reinterpret_cast<const __half*>(tt.wyl), tt.wye,
+      tt.wa, tt.perm, reinterpret_cast<const __half*>(tt.ph), reinterpret_cast<const __half*>(tt.pl),
+      tt.pe, out, nwin, nfreq, tt.n_tied, mx, my, tt.err);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+}  // namespace fftbf
