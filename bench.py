@@ -637,6 +637,21 @@ def run_profile_case(args):
     block = synth.volts(T, nfreq, npol, nx, ny, seed=WL["seed"], sigma=WL["sigma"], sources=src)
     w = synth.separable_weights(synth.half_sine(nx), synth.half_sine(ny))
     u, v = synth.tied_pointings(WL["seed"] + 1, nfreq, n_tied, nx, ny, mx, my)
+    if args.tied:
+        # the tied-beam GEMM at the step's shape on 64 channels: 128 windows of positive
+        # synthetic beams, 2048 pointings (weight tables 268 MB, above L2); twice
+        nw, nf = 128, 64
+        g = torch.Generator(device="cuda")
+        g.manual_seed(WL["seed"] + 9)
+        pb = torch.rand((nw, nf, mx, my), device="cuda", generator=g) + 1.0
+        uu, vv = synth.tied_pointings(WL["seed"] + 1, nf, n_tied, nx, ny, mx, my)
+        out = torch.empty((nw, nf, n_tied), device="cuda")
+        with fb.plan_create(nx, ny, mx, my, npol, nf, n_int, weights=w) as plan:
+            for _ in range(2):
+                fb.tied_beams(plan, pb, nw, n_tied, uu, vv, out)
+            fb.plan_sync(plan)
+        print("profile case (tied) done")
+        return 0
     if args.products:
         # the intensity-space products on 40 windows x 1024 channels of positive synthetic
         # beams (335 MB, above L2): stacked visibilities and localisation, twice each
@@ -685,6 +700,8 @@ def main():
     ap.add_argument("--serve-frames", type=int, default=6000)
     ap.add_argument("--profile-case", action="store_true",
                     help="run a small case of the timed kernels (for ncu) and exit")
+    ap.add_argument("--tied", action="store_true",
+                    help="with --profile-case: the tied-beam GEMM")
     ap.add_argument("--products", action="store_true",
                     help="with --profile-case: the stacked-visibility and localisation kernels")
     args = ap.parse_args()

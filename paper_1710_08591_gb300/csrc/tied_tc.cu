@@ -28,7 +28,7 @@ constexpr int TM = 128, TN = 128, KC = 64;     // pointings, windows, beams per 
 constexpr int LBO = 128, SBO = 1024;           // canonical K-major tile: 8 K blocks per row group
 constexpr int TILE = TM * KC * 2;              // bytes of one 128 x 64 FP16 tile
 constexpr int STAGE = 4 * TILE;                // W hi, W lo, P hi, P lo
-constexpr int NT = 128;
+constexpr int NT = 256;                        // warps w and w + 4 share TMEM lane quarter w % 4
 constexpr int NS = 3;                          // staging buffers
 constexpr int MAXA = 4;                        // E-W beams (one accumulator each)
 constexpr uint32_t TMEM_COLS = 512;
@@ -116,11 +116,12 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
     s_mask = 0;
   }
   __syncthreads();
-  const int s = s0 + tid;
+  const int row = tid & (ttc::TM - 1);           // TMEM lane / pointing of this thread
+  const int s = s0 + row;
   const bool srow = s < n_tied;
   const int my_a = srow ? wa[fs0 + s] : 0;
   const int my_e = srow ? wye[fs0 + s] : 0;
-  if (srow) atomicOr(&s_mask, 1 << my_a);
+  if (srow && tid < ttc::TM) atomicOr(&s_mask, 1 << my_a);
   __syncthreads();
   const int mask = s_mask;
   int nact = 0, my_ai = 0;
@@ -155,23 +156,32 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
       if ((mask >> a) & 1 && ++c == want) A = a;
     return A;
   };
+  // this thread stages 16-byte chunk kb of rows r0 + 32 ii (ii < 4) of each of the four tiles;
+  // the row offsets are fixed for the whole CTA (the beam rows move by A my per E-W beam)
+  const int r0 = tid >> 3, kb = tid & 7;
+  const uint32_t dbase = tc::kmajor_off(r0, kb * 8, ttc::LBO, ttc::SBO);   // + 4096 ii
+  int64_t wrow[4], prow[4];
+  bool wv[4], pv[4];
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii) {
+    const int r = r0 + 32 * ii;
+    wv[ii] = s0 + r < n_tied;
+    wrow[ii] = wv[ii] ? (fs0 + s0 + r) * my + kb * 8 : 0;
+    pv[ii] = j0 + r < nwin;
+    prow[ii] = pv[ii] ? ((j0 + r) * nfreq + f) * (int64_t)mx * my + kb * 8 : 0;
+  }
   auto load = [&](int t) {
-    unsigned char* stg = smem_t + (t % ttc::NS) * ttc::STAGE;
-    const int A = chunk_beam(t), kc = t % kcs;
-    for (int idx = tid; idx < 4 * ttc::TM * 8; idx += ttc::NT) {
-      const int tile = idx >> 10, r = (idx >> 3) & 127, kb = idx & 7;
-      unsigned char* dst = stg + tile * ttc::TILE + tc::kmajor_off(r, kb * 8, ttc::LBO, ttc::SBO);
-      const int k0 = kc * ttc::KC + kb * 8;
-      if (tile < 2) {
-        const bool v = s0 + r < n_tied;
-        const __half* src = (tile == 0 ? wyh : wyl) + (v ? (fs0 + s0 + r) * my + k0 : 0);
-        cp_async16_z(dst, src, v);
-      } else {
-        const int64_t j = j0 + r;
-        const bool v = j < nwin;
-        const __half* src = (tile == 2 ? ph : pl) + (v ? ((j * nfreq + f) * mx + A) * my + k0 : 0);
-        cp_async16_z(dst, src, v);
-      }
+    unsigned char* stg = smem_t + (t % ttc::NS) * ttc::STAGE + dbase;
+    const int A = chunk_beam(t);
+    const int64_t k0 = (int64_t)(t % kcs) * ttc::KC;
+    const int64_t pk = (int64_t)A * my + k0;
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      unsigned char* d = stg + 4096 * ii;
+      cp_async16_z(d, wyh + (wv[ii] ? wrow[ii] + k0 : 0), wv[ii]);
+      cp_async16_z(d + ttc::TILE, wyl + (wv[ii] ? wrow[ii] + k0 : 0), wv[ii]);
+      cp_async16_z(d + 2 * ttc::TILE, ph + (pv[ii] ? prow[ii] + pk : 0), pv[ii]);
+      cp_async16_z(d + 3 * ttc::TILE, pl + (pv[ii] ? prow[ii] + pk : 0), pv[ii]);
     }
   };
   for (int t = 0; t < ttc::NS - 1; ++t) {         // prologue: NS - 1 groups (empty past the end)
@@ -220,9 +230,10 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
   }
   tc::fence_after_sync();
   if (ok && total > 0) {
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pointings) and windows 64 (w / 4) .. + 63
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int dst_s = srow ? perm[fs0 + s] : 0;
-    for (int c = 0; c < ttc::TN / 32; ++c) {
+    for (int c = 2 * (warp >> 2); c < 2 * (warp >> 2) + 2; ++c) {
       for (int a2 = 0; a2 < nact; ++a2) {
         uint32_t r[32];
         tc::tmem_ld32(tbase + lane_off + (uint32_t)(a2 * ttc::TN + 32 * c), r);
@@ -231,9 +242,13 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             const int64_t j = j0 + 32 * c + q;
-            if (j < nwin)
+            if (j < nwin) {
+              // D 2^-E: a power-of-two product (exact) while 2^-E is a normal float
+              const int E = my_e + s_pe[a2][32 * c + q];
+              const float d = __uint_as_float(r[q]);
               out[(j * nfreq + f) * (int64_t)n_tied + dst_s] =
-                  ldexpf(__uint_as_float(r[q]), -(my_e + s_pe[a2][32 * c + q]));
+                  (E > -127 && E < 127) ? d * __int_as_float((127 - E) << 23) : ldexpf(d, -E);
+            }
           }
         }
       }
