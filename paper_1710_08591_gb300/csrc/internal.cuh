@@ -124,6 +124,7 @@ struct TiedTables {
   // tensor-core path (E-W axis on the grid): split FP16 weight rows and their exponents,
   // the E-W beam of each sorted pointing, and per-call split beam rows
   int tc = 0;
+  int tc_n_tied = 0;            // pointings per channel of the split tables
   uint16_t* wyh = nullptr;      // [nfreq][n_tied][my] FP16 hi of 2^e wx wy
   uint16_t* wyl = nullptr;      // [nfreq][n_tied][my] FP16 lo
   int* wye = nullptr;           // [nfreq][n_tied] row exponent e

@@ -628,6 +628,7 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
     if (rc != FFTBF_OK) return rc;
     tt.tc = 0;
     if (tied_tc_eligible(dense_x, mx, my)) {
+      tt.tc_n_tied = n_tied;
       rc = tied_tc_build(tt, (int64_t)nuv, mx, my, st);
       if (rc != FFTBF_OK) return rc;
     }

@@ -46,49 +46,84 @@ __device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool 
 // e such that 2^e m lies in [2^14, 2^15) (0 for a zero row)
 __device__ __forceinline__ int split_exp(float m) { return m > 0.f ? 14 - ilogbf(m) : 0; }
 
-// Split rows of x (one warp per row): hi, lo and the row exponent.
-__device__ __forceinline__ void split_row(const float* x, float scale_in, int n, __half* hi,
-                                          __half* lo, int* e_out, int lane) {
+// Half offset of element (row r < 128, k) of a row tile: tile (k / 64) of the row tile's
+// chunks, canonical K-major layout inside.
+__device__ __forceinline__ int64_t tiled_off(int64_t tile0, int r, int k) {
+  return (tile0 + (k >> 6)) * (ttc::TILE / 2) +
+         (int64_t)(tc::kmajor_off(r, k & 63, ttc::LBO, ttc::SBO) >> 1);
+}
+
+// Split one row x (one warp): hi and lo written at tiled_off(tile0, r, k), the row exponent
+// returned; a null x writes a zero row.
+__device__ __forceinline__ int split_row_tiled(const float* x, float scale_in, int n, __half* hi,
+                                               __half* lo, int64_t tile0, int r, int lane) {
   float m = 0.f;
-  for (int b = lane; b < n; b += 32) m = fmaxf(m, fabsf(scale_in * x[b]));
+  if (x)
+    for (int b = lane; b < n; b += 32) m = fmaxf(m, fabsf(scale_in * x[b]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int e = split_exp(m);
   for (int b = lane; b < n; b += 32) {
-    const float v = ldexpf(scale_in * x[b], e);
+    const float v = x ? ldexpf(scale_in * x[b], e) : 0.f;
     const __half h = __float2half_rn(v);
-    hi[b] = h;
-    lo[b] = __float2half_rn(v - __half2float(h));
+    const int64_t o = tiled_off(tile0, r, b);
+    hi[o] = h;
+    lo[o] = __float2half_rn(v - __half2float(h));
   }
-  if (lane == 0) *e_out = e;
+  return e;
 }
 
-// Weight tables (sorted pointing order): the row's E-W beam A_s (the largest |wx|) and the
-// split of wx[s, A_s] wy[s, :].
+// Weight tables in tiles: per channel, pointing tiles of 128 sorted slots (zero rows past
+// n_tied), each [my / 64] chunks of 128 x 64. Also the row's E-W beam A_s (the largest
+// |wx|) and exponent; the row is wx[s, A_s] wy[s, :].
 __global__ void tied_tc_table_kernel(const float* __restrict__ wx, const float* __restrict__ wy,
-                                     int64_t nrows, int mx, int my, __half* wyh, __half* wyl,
-                                     int* wye, int* wa) {
+                                     int nfreq, int n_tied, int mx, int my, __half* wyh,
+                                     __half* wyl, int* wye, int* wa) {
   const int lane = threadIdx.x & 31;
+  const int nts = (n_tied + ttc::TM - 1) / ttc::TM, kcs = my / ttc::KC;
+  const int64_t nrows = (int64_t)nfreq * nts * ttc::TM;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nw) {
+  for (int64_t rp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rp < nrows; rp += nw) {
+    const int f = (int)(rp / ((int64_t)nts * ttc::TM));
+    const int slot = (int)(rp - (int64_t)f * nts * ttc::TM);
+    const int64_t tile0 = ((int64_t)f * nts + (slot >> 7)) * kcs;
+    if (slot >= n_tied) {
+      split_row_tiled(nullptr, 0.f, my, wyh, wyl, tile0, slot & 127, lane);
+      continue;
+    }
+    const int64_t r = (int64_t)f * n_tied + slot;
     int A = 0;
     float best = -1.f;
     for (int a = 0; a < mx; ++a) {
       const float v = fabsf(wx[r * mx + a]);
       if (v > best) { best = v; A = a; }
     }
-    split_row(wy + r * my, wx[r * mx + A], my, wyh + r * my, wyl + r * my, wye + r, lane);
-    if (lane == 0) wa[r] = A;
+    const int e = split_row_tiled(wy + r * my, wx[r * mx + A], my, wyh, wyl, tile0, slot & 127, lane);
+    if (lane == 0) {
+      wye[r] = e;
+      wa[r] = A;
+    }
   }
 }
 
-// Beam rows P[j, f, A, :] split the same way (per call).
-__global__ void tied_tc_prep_kernel(const float* __restrict__ P, int64_t nrows, int my,
-                                    __half* ph, __half* pl, int* pe) {
+// Beam rows P[j, f, A, :] split the same way (per call), in tiles per (channel, E-W beam) of
+// 128 windows (zero rows past nwin); exponents at pe[(j nfreq + f) mx + A].
+__global__ void tied_tc_prep_kernel(const float* __restrict__ P, int64_t nwin, int nfreq, int mx,
+                                    int my, __half* ph, __half* pl, int* pe) {
   const int lane = threadIdx.x & 31;
+  const int ntj = (int)((nwin + ttc::TN - 1) / ttc::TN), kcs = my / ttc::KC;
+  const int64_t per_fa = (int64_t)ntj * ttc::TN;
+  const int64_t nrows = (int64_t)nfreq * mx * per_fa;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nw)
-    split_row(P + r * my, 1.f, my, ph + r * my, pl + r * my, pe + r, lane);
+  for (int64_t rp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); rp < nrows; rp += nw) {
+    const int64_t fa = rp / per_fa;                 // f mx + A
+    const int64_t j = rp - fa * per_fa;
+    const int f = (int)(fa / mx), A = (int)(fa - (int64_t)f * mx);
+    const int64_t tile0 = (fa * ntj + (j >> 7)) * kcs;
+    const float* x = j < nwin ? P + ((j * nfreq + f) * mx + A) * my : nullptr;
+    const int e = split_row_tiled(x, 1.f, my, ph, pl, tile0, (int)(j & 127), lane);
+    if (x && lane == 0) pe[(j * nfreq + f) * mx + A] = e;
+  }
 }
 
 __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
@@ -97,7 +132,7 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
     const __half* __restrict__ pl, const int* __restrict__ pe, float* __restrict__ out,
     int64_t nwin, int nfreq, int n_tied, int mx, int my, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_t[];
-  __shared__ uint64_t bars[ttc::NS];
+  __shared__ uint64_t full[ttc::NS], empty[ttc::NS];
   __shared__ uint32_t taddr;
   __shared__ int s_mask;
   __shared__ int s_pe[ttc::MAXA][ttc::TN];
@@ -111,7 +146,10 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < ttc::NS; ++i) tc::mbar_init(&bars[i], 1);
+    for (int i = 0; i < ttc::NS; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
     tc::mbar_init_fence();
     s_mask = 0;
   }
@@ -146,56 +184,39 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
   const int kcs = my / ttc::KC;
   const int total = nact * kcs;
   const uint32_t idesc = tc::idesc_f16(ttc::TM, ttc::TN, false);
-  bool ok = true;
-  // chunk t = (E-W beam in use number t / kcs, K chunk t % kcs) is staged in buffer t % NS,
-  // NS - 1 chunks ahead of the MMAs; a buffer is refilled once its MMAs have completed
-  auto chunk_beam = [&](int t) {
-    const int want = t / kcs;
-    int A = 0;
-    for (int a = 0, c = -1; a < mx; ++a)
-      if ((mask >> a) & 1 && ++c == want) A = a;
-    return A;
-  };
-  // this thread stages 16-byte chunk kb of rows r0 + 32 ii (ii < 4) of each of the four tiles;
-  // the row offsets are fixed for the whole CTA (the beam rows move by A my per E-W beam)
-  const int r0 = tid >> 3, kb = tid & 7;
-  const uint32_t dbase = tc::kmajor_off(r0, kb * 8, ttc::LBO, ttc::SBO);   // + 4096 ii
-  int64_t wrow[4], prow[4];
-  bool wv[4], pv[4];
-#pragma unroll
-  for (int ii = 0; ii < 4; ++ii) {
-    const int r = r0 + 32 * ii;
-    wv[ii] = s0 + r < n_tied;
-    wrow[ii] = wv[ii] ? (fs0 + s0 + r) * my + kb * 8 : 0;
-    pv[ii] = j0 + r < nwin;
-    prow[ii] = pv[ii] ? ((j0 + r) * nfreq + f) * (int64_t)mx * my + kb * 8 : 0;
-  }
-  auto load = [&](int t) {
-    unsigned char* stg = smem_t + (t % ttc::NS) * ttc::STAGE + dbase;
-    const int A = chunk_beam(t);
-    const int64_t k0 = (int64_t)(t % kcs) * ttc::KC;
-    const int64_t pk = (int64_t)A * my + k0;
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii) {
-      unsigned char* d = stg + 4096 * ii;
-      cp_async16_z(d, wyh + (wv[ii] ? wrow[ii] + k0 : 0), wv[ii]);
-      cp_async16_z(d + ttc::TILE, wyl + (wv[ii] ? wrow[ii] + k0 : 0), wv[ii]);
-      cp_async16_z(d + 2 * ttc::TILE, ph + (pv[ii] ? prow[ii] + pk : 0), pv[ii]);
-      cp_async16_z(d + 3 * ttc::TILE, pl + (pv[ii] ? prow[ii] + pk : 0), pv[ii]);
-    }
-  };
-  for (int t = 0; t < ttc::NS - 1; ++t) {         // prologue: NS - 1 groups (empty past the end)
-    if (t < total) load(t);
-    cp_async_commit();
-  }
-  for (int t = 0; t < total; ++t) {
-    cp_async_wait<ttc::NS - 2>();                 // chunk t has landed
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
+  // Thread 0 runs the pipeline: chunk t = (E-W beam in use number t / kcs, K chunk t % kcs)
+  // goes to stage t % NS as four 16 KB bulk copies completing on full[stage]; its MMAs
+  // commit to empty[stage], after which the stage takes chunk t + NS. The other threads wait
+  // at the CTA barrier. Every wait is bounded.
+  __shared__ int s_ok;
+  if (tid == 0) {
+    bool ok = true;
+    const int nts = (n_tied + ttc::TM - 1) / ttc::TM;
+    const int ntj = (int)((nwin + ttc::TN - 1) / ttc::TN);
+    const int64_t wt0 = ((int64_t)f * nts + blockIdx.x) * kcs;   // first weight tile
+    auto issue = [&](int t) {
+      const int st = t % ttc::NS;
+      unsigned char* stg = smem_t + st * ttc::STAGE;
+      const int ai = t / kcs, kc = t - ai * kcs;
+      int A = 0;
+      for (int a = 0, c = -1; a < mx; ++a)
+        if ((mask >> a) & 1 && ++c == ai) A = a;
+      const int64_t pt = (((int64_t)f * mx + A) * ntj + blockIdx.y) * kcs + kc;
+      const int64_t wt = wt0 + kc;
+      tc::mbar_arrive_expect_tx(&full[st], (uint32_t)ttc::STAGE);
+      tc::bulk_g2s(stg, wyh + wt * (ttc::TILE / 2), ttc::TILE, &full[st]);
+      tc::bulk_g2s(stg + ttc::TILE, wyl + wt * (ttc::TILE / 2), ttc::TILE, &full[st]);
+      tc::bulk_g2s(stg + 2 * ttc::TILE, ph + pt * (ttc::TILE / 2), ttc::TILE, &full[st]);
+      tc::bulk_g2s(stg + 3 * ttc::TILE, pl + pt * (ttc::TILE / 2), ttc::TILE, &full[st]);
+    };
+    for (int t = 0; t < ttc::NS && t < total; ++t) issue(t);
+    for (int t = 0; t < total && ok; ++t) {
+      const int st = t % ttc::NS;
+      const uint32_t par = (uint32_t)((t / ttc::NS) & 1);
+      ok = tc::mbar_wait(&full[st], par, ttc::WAIT_NS);
+      if (!ok) break;
       tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(smem_t + (t % ttc::NS) * ttc::STAGE);
+      const uint32_t sa = tc::smem_u32(smem_t + st * ttc::STAGE);
       const uint32_t d = tbase + (uint32_t)((t / kcs) * ttc::TN);
       const int kc = t % kcs;
 #pragma unroll
@@ -209,25 +230,23 @@ __global__ void __launch_bounds__(ttc::NT, 1) tied_tc_kernel(
         tc::mma_f16(d, dwh, dpl, idesc, 1u);
         tc::mma_f16(d, dwl, dph, idesc, 1u);
       }
-      tc::mma_commit(&bars[t % ttc::NS]);
-    }
-    const int tn = t + ttc::NS - 1;               // next chunk to stage, into buffer (t - 1) % NS
-    if (tn < total) {
-      if (t >= 1) {
-        ok = tc::mbar_wait(&bars[(t - 1) % ttc::NS], (uint32_t)(((t - 1) / ttc::NS) & 1), ttc::WAIT_NS);
-        if (!__syncthreads_and(ok)) break;
+      tc::mma_commit(&empty[st]);
+      // refill the stage of chunk t - 1 once its MMAs are done
+      const int tp = t - 1;
+      if (tp >= 0 && tp + ttc::NS < total) {
+        ok = tc::mbar_wait(&empty[tp % ttc::NS], (uint32_t)((tp / ttc::NS) & 1), ttc::WAIT_NS);
+        if (ok) issue(tp + ttc::NS);
       }
-      load(tn);
     }
-    cp_async_commit();
+    if (ok && total > 0) {                          // the last commit covers every MMA
+      const int tl = total - 1;
+      ok = tc::mbar_wait(&empty[tl % ttc::NS], (uint32_t)((tl / ttc::NS) & 1), ttc::WAIT_NS);
+    }
+    s_ok = ok ? 1 : 0;
   }
-  cp_async_wait<0>();                             // no copy left in flight (also on a timeout)
-  // the last commit covers every MMA of the CTA
-  if (ok && total > 0) {
-    const int tl = total - 1;
-    ok = tc::mbar_wait(&bars[tl % ttc::NS], (uint32_t)((tl / ttc::NS) & 1), ttc::WAIT_NS);
-    ok = __syncthreads_and(ok);
-  }
+  tc::fence_before_sync();
+  __syncthreads();
+  const bool ok = s_ok != 0;
   tc::fence_after_sync();
   if (ok && total > 0) {
     // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pointings) and windows 64 (w / 4) .. + 63
@@ -275,16 +294,21 @@ int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st) 
   cudaFree(tt.wa);
   tt.wyh = tt.wyl = nullptr;
   tt.wye = tt.wa = nullptr;
-  bool ok = cudaMalloc(&tt.wyh, nuv * my * sizeof(__half)) == cudaSuccess &&
-            cudaMalloc(&tt.wyl, nuv * my * sizeof(__half)) == cudaSuccess &&
+  const int n_tied = tt.tc_n_tied;
+  const int nfreq = (int)(nuv / n_tied);
+  const int64_t nts = (n_tied + ttc::TM - 1) / ttc::TM;
+  const size_t halves = (size_t)nfreq * nts * ttc::TM * my;      // padded to whole tiles
+  bool ok = cudaMalloc(&tt.wyh, halves * sizeof(__half)) == cudaSuccess &&
+            cudaMalloc(&tt.wyl, halves * sizeof(__half)) == cudaSuccess &&
             cudaMalloc(&tt.wye, nuv * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&tt.wa, nuv * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return set_error(FFTBF_ENOMEM, "cannot allocate the split tied-beam tables");
   }
-  const unsigned blocks = (unsigned)std::min<int64_t>((nuv + 7) / 8, 1 << 20);
-  tied_tc_table_kernel<<<blocks, 256, 0, st>>>(tt.wx, tt.wy, nuv, mx, my,
+  const int64_t rows = (int64_t)nfreq * nts * ttc::TM;
+  const unsigned blocks = (unsigned)std::min<int64_t>((rows + 7) / 8, 1 << 20);
+  tied_tc_table_kernel<<<blocks, 256, 0, st>>>(tt.wx, tt.wy, nfreq, n_tied, mx, my,
                                                reinterpret_cast<__half*>(tt.wyh),
                                                reinterpret_cast<__half*>(tt.wyl), tt.wye, tt.wa);
   FFTBF_CUDA_TRY(cudaGetLastError());
@@ -294,8 +318,12 @@ int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st) 
 
 int tied_tc_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int mx, int my,
                    float* out, cudaStream_t st) {
-  const int64_t nrows = nwin * nfreq * mx;
-  if ((size_t)nrows > tt.p_cap) {
+  const int64_t ntj = (nwin + ttc::TN - 1) / ttc::TN;
+  if (ntj > 65535 || nfreq > 65535)
+    return set_error(FFTBF_EUNSUPPORTED, "tied beams: too many windows or channels per call");
+  const int64_t prow = (int64_t)nfreq * mx * ntj * ttc::TN;        // padded beam rows
+  const int64_t erow = nwin * nfreq * mx;                           // exponents
+  if ((size_t)prow > tt.p_cap) {
     cudaStreamSynchronize(st);                  // the old scratch may still be read
     cudaFree(tt.ph);
     cudaFree(tt.pl);
@@ -303,26 +331,24 @@ int tied_tc_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, 
     tt.ph = tt.pl = nullptr;
     tt.pe = nullptr;
     tt.p_cap = 0;
-    bool ok = cudaMalloc(&tt.ph, nrows * my * sizeof(__half)) == cudaSuccess &&
-              cudaMalloc(&tt.pl, nrows * my * sizeof(__half)) == cudaSuccess &&
-              cudaMalloc(&tt.pe, nrows * sizeof(int)) == cudaSuccess;
+    bool ok = cudaMalloc(&tt.ph, prow * my * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&tt.pl, prow * my * sizeof(__half)) == cudaSuccess &&
+              cudaMalloc(&tt.pe, std::max<int64_t>(erow, prow) * sizeof(int)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       return set_error(FFTBF_ENOMEM, "cannot allocate the split beam scratch");
     }
-    tt.p_cap = (size_t)nrows;
+    tt.p_cap = (size_t)prow;
   }
-  const unsigned pblocks = (unsigned)std::min<int64_t>((nrows + 7) / 8, 1 << 20);
-  tied_tc_prep_kernel<<<pblocks, 256, 0, st>>>(beams, nrows, my, reinterpret_cast<__half*>(tt.ph),
+  const unsigned pblocks = (unsigned)std::min<int64_t>((prow + 7) / 8, 1 << 20);
+  tied_tc_prep_kernel<<<pblocks, 256, 0, st>>>(beams, nwin, nfreq, mx, my,
+                                               reinterpret_cast<__half*>(tt.ph),
                                                reinterpret_cast<__half*>(tt.pl), tt.pe);
   FFTBF_CUDA_TRY(cudaGetLastError());
-  const int64_t jt = (nwin + ttc::TN - 1) / ttc::TN;
-  if (jt > 65535 || nfreq > 65535)
-    return set_error(FFTBF_EUNSUPPORTED, "tied beams: too many windows or channels per call");
   const size_t smem = ttc::NS * (size_t)ttc::STAGE;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(tied_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  dim3 grid((tt.n_tied + ttc::TM - 1) / ttc::TM, (unsigned)jt, nfreq);
+  dim3 grid((tt.n_tied + ttc::TM - 1) / ttc::TM, (unsigned)ntj, nfreq);
   tied_tc_kernel<<<grid, ttc::NT, smem, st>>>(
       reinterpret_cast<const __half*>(tt.wyh), reinterpret_cast<const __half*>(tt.wyl), tt.wye,
       tt.wa, tt.perm, reinterpret_cast<const __half*>(tt.ph), reinterpret_cast<const __half*>(tt.pl),
