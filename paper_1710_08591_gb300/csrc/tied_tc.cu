@@ -6,18 +6,20 @@
 // each K step accumulates hi*hi + hi*lo + lo*hi in FP32 (tcgen05.mma kind::f16, TMEM), which
 // keeps FP32 accuracy; e scales every weight row and every beam row so that its largest
 // magnitude lies in [2^14, 2^15) (inside the FP16 range, with the residuals normal), and the
-// epilogue divides by 2^(e_s + e_j) exactly. A CTA computes 128 pointings x 128 windows of
-// one channel: K chunks of 64 beams are staged by cp.async (three buffers, two chunks ahead
-// of the MMAs; zero rows past the ends), one TMEM accumulator of 128 columns per E-W
-// beam used by the tile's pointings, and each pointing (TMEM lane) reads its own beam's
-// accumulator. Waits on MMA completion are bounded; a timeout sets the plan's error word.
+// epilogue divides by 2^(e_s + e_j) exactly. Both split operands are stored in global
+// memory already cut into 16 KB tiles (128 rows x 64 beams, the canonical K-major layout,
+// zero rows past the ends). A CTA computes 128 pointings x 128 windows of one channel: one
+// thread stages each K chunk as four bulk copies completing on a full-mbarrier (three
+// stages), issues its MMAs and commits them to the stage's empty-mbarrier; one TMEM
+// accumulator of 128 columns per E-W beam used by the tile's pointings, and each pointing
+// (TMEM lane) reads its own beam's accumulator. Every wait is bounded; a timeout sets the
+// plan's error word.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdlib>
 
-#include "beam_fp32.cuh"
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,14 +36,6 @@ constexpr int MAXA = 4;                        // E-W beams (one accumulator eac
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_NS = 1000000000ull;
 }  // namespace ttc
-
-// 16-byte cp.async that writes zeros instead of reading when !valid
-__device__ __forceinline__ void cp_async16_z(void* smem, const void* gmem, bool valid) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
-               : "memory");
-}
 
 // e such that 2^e m lies in [2^14, 2^15) (0 for a zero row)
 __device__ __forceinline__ int split_exp(float m) { return m > 0.f ? 14 - ilogbf(m) : 0; }
