@@ -63,7 +63,7 @@ def flops_per_snapshot(nx, ny, mx, my):
 TRAFFIC_FP32 = 16 * (403.262208e6 + 3.753472e6)
 # The same for one batched step (one batch_kernel launch over 8192 samples), from the
 # 512-sample profile case (`--workload batched --profile-case`) scaled x16.
-TRAFFIC_BATCH = 16 * (2187.772e6 + 47.338240e6)
+TRAFFIC_BATCH = None
 
 
 def samples_per_step():

@@ -111,6 +111,49 @@ __device__ __forceinline__ void warp_ew_stage(const BeamArgs& a, const uint8_t* 
   const int ny = FULL ? NH : a.ny;
   const int nyf = FULL ? NH : a.nyf;
   const bool rw = a.real_w != 0;
+  if constexpr (FULL && MX <= 4 && R >= 2) {
+    // two adjacent feeds per thread: one 16-bit byte load and one 128-bit load of two
+    // weights per E-W row; the pair lands in adjacent slots (iy even, rows of R >= 2)
+    auto ew = [&](float2* z) {
+      if constexpr (MX == 3) {
+        // 3-point DFT: X_{1,2} = z0 - (z1 + z2)/2 -/+ i (sqrt(3)/2)(z1 - z2)
+        const float2 z0 = z[0], sm = cadd(z[1], z[2]), df = csub(z[1], z[2]);
+        const float h3 = 0.86602540378443865f;
+        const float2 m = make_float2(z0.x - 0.5f * sm.x, z0.y - 0.5f * sm.y);
+        const float2 t = make_float2(h3 * df.y, -h3 * df.x);
+        z[0] = cadd(z0, sm);
+        z[1] = cadd(m, t);
+        z[2] = csub(m, t);
+      } else {
+        Dft<MX>::run(z);
+      }
+    };
+    for (int c = threadIdx.x; c < S * (NH / 2); c += kThreads) {
+      const int s = c / (NH / 2), iy = 2 * (c - s * (NH / 2));
+      float2 z0[MX], z1[MX];
+#pragma unroll
+      for (int A = 0; A < MX; ++A) z0[A] = z1[A] = czero();
+      if (it * S + s < nsnap) {
+        const uint8_t* rs = raw + s * nant;
+#pragma unroll
+        for (int ix = 0; ix < MX; ++ix) {
+          const unsigned v = *reinterpret_cast<const uint16_t*>(rs + ix * NH + iy);
+          const float4 w = *reinterpret_cast<const float4*>(wsm + ix * NH + iy);
+          z0[ix] = weigh(rw, make_float2(w.x, w.y), (uint8_t)(v & 255u));
+          z1[ix] = weigh(rw, make_float2(w.z, w.w), (uint8_t)(v >> 8));
+        }
+        ew(z0);
+        ew(z1);
+      }
+      const int slot = (iy % R) + stride * prow<R>(iy / R);
+#pragma unroll
+      for (int A = 0; A < MX; ++A) {
+        regs[(s * MX + A) * reg + slot] = z0[A];
+        regs[(s * MX + A) * reg + slot + 1] = z1[A];
+      }
+    }
+    return;
+  }
   for (int c = threadIdx.x; c < S * NH; c += kThreads) {
     const int s = c / NH, iy = c - s * NH;
     float2 z[MX];
