@@ -63,7 +63,7 @@ def flops_per_snapshot(nx, ny, mx, my):
 TRAFFIC_FP32 = 16 * (403.262208e6 + 3.753472e6)
 # The same for one batched step (one batch_kernel launch over 8192 samples), from the
 # 512-sample profile case (`--workload batched --profile-case`) scaled x16.
-TRAFFIC_BATCH = None
+TRAFFIC_BATCH = 16 * (2184.420e6 + 36.285184e6)
 
 
 def samples_per_step():
