@@ -298,6 +298,12 @@ int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st) 
             cudaMalloc(&tt.wa, nuv * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
+    cudaFree(tt.wyh);
+    cudaFree(tt.wyl);
+    cudaFree(tt.wye);
+    cudaFree(tt.wa);
+    tt.wyh = tt.wyl = nullptr;
+    tt.wye = tt.wa = nullptr;
     return set_error(FFTBF_ENOMEM, "cannot allocate the split tied-beam tables");
   }
   const int64_t rows = (int64_t)nfreq * nts * ttc::TM;
@@ -330,6 +336,11 @@ int tied_tc_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, 
               cudaMalloc(&tt.pe, std::max<int64_t>(erow, prow) * sizeof(int)) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
+      cudaFree(tt.ph);
+      cudaFree(tt.pl);
+      cudaFree(tt.pe);
+      tt.ph = tt.pl = nullptr;
+      tt.pe = nullptr;
       return set_error(FFTBF_ENOMEM, "cannot allocate the split beam scratch");
     }
     tt.p_cap = (size_t)prow;
