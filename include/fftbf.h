@@ -121,7 +121,14 @@ int fftbf_execute(fftbf_plan* plan, const uint8_t* volts_dev, int64_t T, float* 
  *              caller's choice. Copied.
  *   tied_dev   device float [n_windows][nfreq][n_tied]; overwritten.
  * The weight tables are generated in FP64 on the device, rounded to FP32 and kept in
- * the plan; a later call with identical u, v and n_tied reuses them.
+ * the plan; a later call with identical u, v and n_tied reuses them. When the E-W axis is
+ * on the FFT-beam grid (pad_x < 2 nx - 1, pad_x <= 4) and pad_y is a multiple of 64, the
+ * sum runs on the tensor cores with each operand split into two FP16 parts (three
+ * products per term, FP32 accumulation: FP32 accuracy); the split weight tables are also
+ * kept in the plan. Environment FFTBF_TIED_TC=0 selects the CUDA-core FP32 GEMM, which
+ * is also used when the split tables cannot be allocated.
+ * Errors: FFTBF_EINVAL (arguments, off-grid pointing), FFTBF_ENOMEM (tables),
+ * FFTBF_ETIMEOUT (reported by fftbf_plan_sync if a tensor-core wait ran out).
  */
 int fftbf_tied_beams(fftbf_plan* plan, const float* beams_dev, int64_t n_windows,
                      int n_tied, const double* u, const double* v, float* tied_dev,
