@@ -35,28 +35,36 @@ T_DEV = 3072          # device block per fftbf_execute call (8 windows)
 METRIC = "antenna-samples/s at 4x256 int4 lattice"
 UNIT = "antenna-samples/s"
 # Algorithmic FP32 work of the plain form per snapshot (one pol, one t, one f), counted
-# with 5 N log2 N per complex FFT: apodisation 6/sample, E-W 4-point DFT 16 adds per
-# column, N-S 512-point transform of 256 inputs as two 256-point FFTs plus 256 twiddle
-# products per E-W beam, detection + accumulation 4 flops per beam.
-FLOPS_PER_SNAPSHOT = 6 * 1024 + 16 * 256 + 4 * (2 * 5 * 256 * 8 + 6 * 256) + 4 * 2048
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+# with 5 N log2 N per complex FFT: N-S 512-point transform of 256 inputs as two 256-point
+# FFTs plus 256 twiddle products (6 flops) per E-W beam, E-W 4-point DFT at 5 N log2 N per
+# column, apodisation 2 flops per sample (real weights), detection + accumulation 4 flops
+# per beam: 108,544 flops (106 per antenna-sample).
+FLOPS_PER_SNAPSHOT = 4 * (2 * 5 * 256 * 8 + 6 * 256) + 5 * 4 * 2 * 256 + 2 * 1024 + 4 * 2048
+# Tensor-core form as specified: E-W 4x4 DFT on 256 columns (4096 complex MACs) plus the
+# N-S 512 = 32 x 16 stages (4 x 16384 complex MACs), 8 real flops per complex MAC as
+# real-embedded GEMMs: 544 flops per antenna-sample. As executed (E-W on the CUDA cores):
+# 512 flops per antenna-sample of GEMM.
+TC_FLOPS_SPEC, TC_FLOPS_EXEC = 544.0, 512.0
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
 def flops_per_snapshot(nx, ny, mx, my):
-    """The same count for any lattice with 2x zero-padded N-S axis: apodisation 6/sample,
-    E-W DFT per column (radix-2 counts 5 M log2 M for M = nx a power of two, 8 nx M for a
-    folded DFT matrix), N-S transform of my/2 inputs as two my/2-point FFTs plus my/2
-    twiddle products per E-W beam, detection + accumulation 4 flops per beam."""
+    """The same count for any lattice with 2x zero-padded N-S axis and real weights:
+    apodisation 2/sample, E-W DFT per column (5 M log2 M for M = nx a power of two, 8 nx M
+    for a DFT matrix), N-S transform of my/2 inputs as two my/2-point FFTs plus my/2 twiddle
+    products per E-W beam, detection + accumulation 4 flops per beam."""
     import math
     if mx == 1:
         ew = 0
     elif mx == nx and mx & (mx - 1) == 0:
-        ew = 16 if mx == 4 else (4 if mx == 2 else 5 * mx * int(math.log2(mx)))
+        ew = 5 * mx * int(math.log2(mx))
     else:
         ew = 8 * nx * mx
     h = my // 2
     ns = 2 * 5 * h * int(math.log2(h)) + 6 * h if h > 1 else 6
-    return 6 * nx * ny + ew * ny + mx * ns + 4 * mx * my
+    return 2 * nx * ny + ew * ny + mx * ns + 4 * mx * my
+
+
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
@@ -141,15 +149,16 @@ def host_block(rank=0):
 
 
 def oracle_sample(block, n_chan, chan0=0):
-    """FP64 oracle on one window x n_chan channels x 2 pols; returns (samples, seconds)."""
+    """FP64 oracle on window 0 x n_chan channels x 2 pols; returns (samples, seconds,
+    beams [n_chan][pad_x][pad_y])."""
     import oracle
     w = synth.separable_weights(synth.half_sine(WL["nx"]), synth.half_sine(WL["ny"]))
     v = np.ascontiguousarray(block[:WL["n_int"], chan0:chan0 + n_chan])
     t0 = time.perf_counter()
-    oracle.beams(v, WL["nx"], WL["ny"], WL["pad_x"], WL["pad_y"], WL["npol"], n_chan,
-                 WL["n_int"], weights=w.astype(np.complex128))
+    P = oracle.beams(v, WL["nx"], WL["ny"], WL["pad_x"], WL["pad_y"], WL["npol"], n_chan,
+                     WL["n_int"], weights=w.astype(np.complex128))
     dt = time.perf_counter() - t0
-    return v.size, dt
+    return v.size, dt, P[0]
 
 
 def cpu_cores():
@@ -162,20 +171,57 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(block, budget_s=12.0):
+    """The oracle timed on window 0 of the workload, channel by channel from 0, for about
+    budget_s seconds. Returns the baseline line and the oracle's beams of the channels it
+    covered (window 0), against which every GPU form's beams are then compared."""
     n_chan, tot_s, tot_n, used = 2, 0.0, 0, 0
     chan = 0
+    ref = []
     while tot_s < budget_s and chan + n_chan <= WL["nfreq"]:
-        n, dt = oracle_sample(block, n_chan, chan)
+        n, dt, P = oracle_sample(block, n_chan, chan)
+        ref.append(P)
         tot_s += dt
         tot_n += n
         chan += n_chan
         used += n_chan
         n_chan = min(n_chan * 2, 32)
-    return {"value": tot_n / tot_s, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+    line = {"value": tot_n / tot_s, "unit": UNIT, "cores": cpu_cores(), "cpu_model": cpu_model(),
+            "nproc": os.cpu_count(), "kind": "oracle",
             "sample": f"1 window of 384 samples x {used} channels x 2 pols of the 4x256 "
                       f"workload ({tot_n:.3g} antenna-samples, {tot_s:.1f} s), FP64 numpy "
                       "separable direct DFT"}
+    return line, np.concatenate(ref, axis=0)
+
+
+def form_errors(got, ref):
+    """Per-beam relative error |P - P_ref| / P_ref of a form's window-0 beams against the
+    oracle's, over the channels the oracle covered: max and rms."""
+    n = min(got.shape[0], ref.shape[0])
+    rel = np.abs(got[:n].astype(np.float64) - ref[:n]) / ref[:n]
+    return {"max_rel_err_vs_oracle": float(rel.max()),
+            "rms_rel_err_vs_oracle": float(np.sqrt(np.mean(rel ** 2))),
+            "checked": f"window 0, channels 0-{n - 1}, {rel.size} beams"}
 
 
 def run_reference(args, rank, world):
@@ -187,7 +233,7 @@ def run_reference(args, rank, world):
         oracle_sample(block, n_chan)
     times, ns = [], 0
     for k in range(args.steps):
-        n, dt = oracle_sample(block, n_chan, (k * n_chan) % WL["nfreq"])
+        n, dt, _ = oracle_sample(block, n_chan, (k * n_chan) % WL["nfreq"])
         times.append(dt)
         ns += n
     val = ns / sum(times)
@@ -199,6 +245,7 @@ def run_reference(args, rank, world):
                                    "N-S padded to 512, n_int 384, half-sine weights",
                        "step_sample": f"1 window x {n_chan} channels x 2 pols per step"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                              "sample": f"1 window x {n_chan} channels x 2 pols per step"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -320,38 +367,72 @@ def run_ours(args, rank, world, local_rank):
                "statistic": "median over steps",
                "api": "fftbf_execute_host (pinned host buffers)"}
 
-    # ---- roofline of the dominant kernel (the fused beam kernel)
+    # ---- window-0 beams of the first channels, kept for the error check against the
+    # oracle beams that the CPU-baseline leg computes
+    n_chk = 64
+    kept = {args.form: beams[0, :n_chk].cpu().numpy()}
+
+    # ---- measured FP32 peak: FFMA and packed FFMA2 probes at full occupancy
     peaks, src = measured_peaks()
+    fp32 = fp32_peak(fb, torch, dev, stream)
+    fp32_pk = max(fp32["ffma_tflops"], fp32["ffma2_tflops"])
+
+    # ---- roofline of the dominant kernel (the fused beam kernel)
     k_ms = sum(kern_ms) / len(kern_ms)
     samples_launch = T_DEV * nfreq * npol * nx * ny
     snaps_launch = T_DEV * nfreq * npol
     bytes_launch = samples_launch + wpc * nfreq * mx * my * 4
-    if args.form == "fp32":
-        flops = FLOPS_PER_SNAPSHOT * snaps_launch
-        achieved = flops / (k_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_FP32,
-                "kernel": "beams_fp32_n512_kernel<4, true>", "ms_per_launch": k_ms,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+    flops = FLOPS_PER_SNAPSHOT * snaps_launch
+    achieved = flops / (k_ms / 1e3) / 1e12
+    tpk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    tpk_src = (src + " bf16 sustained (a seconds-long loop under the power cap; FP16 runs at "
+               "the same rate); the beam kernel runs inside a seconds-long step")
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_pk, "unit": "TFLOP/s",
+            "frac": achieved / fp32_pk, "traffic": TRAFFIC_FP32,
+            "kernel": "beams_fp32_n512_kernel<4, true>", "ms_per_launch": k_ms,
+            "flops_per_snapshot": FLOPS_PER_SNAPSHOT,
+            "peak_source": "measured: " + fp32["source"],
+            "fp32_probe": fp32,
+            "frac_of_nominal": achieved / FP32_PEAK_NOMINAL,
+            "nominal_peak": FP32_PEAK_NOMINAL,
+            "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
+                    "peak_gbs": peaks["hbm_gbs"],
+                    "frac": bytes_launch / (k_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                    "peak_source": src}}
+
+    if args.form != "fp32":
+        rate = samples_launch / (k_ms / 1e3)
+        tfl = TC_FLOPS_SPEC * rate / 1e12
+        roof = {"bound": "tensor", "achieved": tfl, "peak": tpk, "unit": "TFLOP/s",
+                "frac": tfl / tpk, "traffic": None, "kernel": "beams_tc_kernel",
+                "ms_per_launch": k_ms, "flops_per_sample": TC_FLOPS_SPEC, "peak_source": tpk_src,
                 "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
                         "peak_gbs": peaks["hbm_gbs"],
                         "frac": bytes_launch / (k_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                         "peak_source": src}}
-    else:
-        roof = {"bound": "tensor", "achieved": None, "peak": peaks["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
 
-    # ---- the tensor-core forms on the same workload (same step, fewer timed steps)
-    forms = {"fp32": {"value": value, "ms_per_step": ms_step}}
-    if not args.no_forms and args.form == "fp32":
+    # ---- the other forms on the same workload (same step, fewer timed steps); each beam
+    # launch is bracketed by CUDA events on the launching stream, as the main form's
+    forms = {args.form: {"value": value, "ms_per_step": ms_step, "beam_ms_per_launch": k_ms,
+                         "beam_antenna_samples_per_s": samples_launch / (k_ms / 1e3)}}
+    if not args.no_forms:
         for form, prec in (("tc_fp16", fb.PREC_TC_FP16), ("tc_bf16", fb.PREC_TC_BF16),
                            ("tc_fp16x3", fb.PREC_TC_FP16X3)):
+            if form == args.form:
+                continue
             fplan = fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w)
             fb.plan_set_precision(fplan, prec)
+            fsteps = max(2, min(args.steps, 5))
+            fev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    for _ in range(ncall)] for _ in range(fsteps)]
 
-            def fstep():
+            def fstep(k=None):
                 for c in range(ncall):
+                    if k is not None:
+                        fev[k][c][0].record(stream)
                     fb.execute(fplan, dvol, T_DEV, beams[c * wpc:(c + 1) * wpc], stream)
+                    if k is not None:
+                        fev[k][c][1].record(stream)
                 fb.tied_beams(fplan, beams, nwin, n_tied, u, v, tied, stream)
 
             for _ in range(max(3, args.warmup)):
@@ -359,29 +440,39 @@ def run_ours(args, rank, world, local_rank):
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             f0.record(stream)
-            fsteps = max(2, min(args.steps, 5))
-            for _ in range(fsteps):
-                fstep()
+            for k in range(fsteps):
+                fstep(k)
             f1.record(stream)
             torch.cuda.synchronize(dev)
             fms = f0.elapsed_time(f1) / fsteps
-            forms[form] = {"value": samples_per_step() * world / (fms / 1e3), "ms_per_step": fms}
-            # the beam kernel of the form: the step less the FP32 step's tied-beam share, per
-            # launch, against the tensor roof as specified (512 flops per antenna-sample as
-            # real-embedded GEMMs, 3x for the split form) and against HBM (1.0104 B per sample)
-            tied_ms = max(0.0, ms_step - ncall * (sum(kern_ms) / len(kern_ms)))
-            b_ms = (fms - tied_ms) / ncall
-            sl = T_DEV * nfreq * npol * nx * ny
-            tf = (1536.0 if form == "tc_fp16x3" else 512.0) * sl / (b_ms / 1e3) / 1e12
-            gb = 1.0104 * sl / (b_ms / 1e3) / 1e9
-            pk, psrc = measured_peaks()
-            forms[form]["roofline"] = {
-                "kernel": "beams_tc_kernel", "ms_per_launch": b_ms,
-                "tensor": {"achieved": tf, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                           "frac": tf / pk["bf16_tflops"], "peak_source": psrc + " bf16 burst (fp16 the same rate)"},
-                "hbm": {"achieved": gb, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": gb / pk["hbm_gbs"], "peak_source": psrc}}
+            b_ms = float(np.mean([a_.elapsed_time(b_) for row in fev for a_, b_ in row]))
+            rate = samples_launch / (b_ms / 1e3)
+            spec = TC_FLOPS_SPEC * rate / 1e12
+            exe = TC_FLOPS_EXEC * rate / 1e12
+            gb = bytes_launch / (b_ms / 1e3) / 1e9
+            forms[form] = {
+                "value": samples_per_step() * world / (fms / 1e3), "ms_per_step": fms,
+                "beam_ms_per_launch": b_ms, "beam_antenna_samples_per_s": rate,
+                "roofline": {
+                    "kernel": "beams_tc_kernel", "bound": "tensor", "ms_per_launch": b_ms,
+                    "timing": "CUDA events around each beam launch on its stream",
+                    "tensor_as_specified": {"flops_per_sample": TC_FLOPS_SPEC, "achieved": spec,
+                                            "peak": tpk, "unit": "TFLOP/s", "frac": spec / tpk,
+                                            "peak_source": tpk_src},
+                    "tensor_as_executed": {"flops_per_sample": TC_FLOPS_EXEC, "achieved": exe,
+                                           "peak": tpk, "unit": "TFLOP/s", "frac": exe / tpk,
+                                           "note": "E-W DFT on the CUDA cores; useful flops"
+                                                   + ("; the split form issues 3 products per "
+                                                      "MAC (1536 tensor flops per sample)"
+                                                      if form == "tc_fp16x3" else "")},
+                    "hbm": {"achieved": gb, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": gb / peaks["hbm_gbs"], "peak_source": src}}}
+            kept[form] = beams[0, :n_chk].cpu().numpy()
             fplan.close()
+        # the step's FP32 beams back in the buffer for the tied-beam variants below
+        for c in range(ncall):
+            fb.execute(plan, dvol, T_DEV, beams[c * wpc:(c + 1) * wpc], stream)
+        torch.cuda.synchronize(dev)
 
     # ---- tied-beam variants on the step's 128 windows: plain (Dirichlet, GEMM over the 512
     # N-S beams), optimal half-sine window (GEMM), the same window truncated to 5 taps
@@ -408,12 +499,14 @@ def run_ours(args, rank, world, local_rank):
             tfl = 2.0 * nwin * nfreq * n_tied * k_ns / (tms / 1e3) / 1e12
             if trunc:                      # the gather kernel, on the CUDA cores
                 tied_forms[name] = {"ms": tms, "tflops": tfl, "path": "CUDA cores",
-                                    "frac_fp32_peak": tfl / FP32_PEAK_TFLOPS}
+                                    "frac_fp32_peak": tfl / fp32_pk}
             else:                          # split-FP16 GEMM: 3 tensor-core products per MAC
                 pk, _ = measured_peaks()
                 tied_forms[name] = {"ms": tms, "tflops": tfl,
                                     "path": "tensor cores, split FP16 (3 products per MAC)",
-                                    "frac_tensor_peak": 3.0 * tfl / pk["bf16_tflops"]}
+                                    "frac_tensor_peak_issued": 3.0 * tfl / pk["bf16_tflops"],
+                                    "frac_tensor_peak_useful": tfl / pk["bf16_tflops"],
+                                    "peak_source": "measured bf16 burst (a few-ms kernel timed alone)"}
             if name == "window_gemm":
                 ref_dense = tied.clone()
             if name.endswith("tap"):
@@ -456,13 +549,29 @@ def run_ours(args, rank, world, local_rank):
                                   "frac_hbm": lbytes / (lms / 1e3) / 1e9 / peaks["hbm_gbs"]}
         del loc
 
+    # ---- the batched uneven-lattice configuration (12 arrays, one persistent launch)
+    batched = None
+    if not args.no_forms and world == 1:
+        batched = batched_form(fb, torch, dev, steps=max(3, min(args.steps, 10)),
+                               warmup=max(3, args.warmup), fp32_pk=fp32_pk)
+
     serving = None
     if not args.no_serving:
-        serving = run_serving(fb, torch, dev, frames_total=args.serve_frames)
+        serving = run_serving(fb, torch, dev, frames_total=args.serve_frames, rate=SERVE["rate"])
+        sweep = []
+        for rate in SERVE["sweep"]:
+            r = run_serving(fb, torch, dev, frames_total=args.serve_frames, rate=rate)
+            sweep.append({k: r[k] for k in ("offered_rate_fps", "achieved_fps", "frames",
+                                            "antenna_samples_per_s", "p50_ms", "p99_ms",
+                                            "max_ms", "frames_per_launch",
+                                            "max_frames_per_launch", "peak_inflight")})
+        serving["sweep"] = sweep
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(block)
+        cpu, ref = cpu_baseline(block)
+        for form, got in kept.items():
+            forms[form].update(form_errors(got, ref))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -480,7 +589,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"{world} GPU(s), independent channel bands per GPU"},
             "gpu_launches": (ncall + 1) * args.steps,
             "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "forms": forms, "tied_beams": tied_forms, "serving": serving}
+            "forms": forms, "batched": batched, "tied_beams": tied_forms, "serving": serving}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -490,11 +599,40 @@ def run_ours(args, rank, world, local_rank):
 
 
 SERVE = dict(lattices=[(4, 256), (8, 64), (16, 16)], nfreq=16, n_int=384, npol=2, streams=64,
-             rate=2000.0, budget=40 << 30, seed=5)
+             rate=2000.0, sweep=[8000.0, 16000.0, 32000.0], budget=40 << 30, seed=5)
 
 
-def run_serving(fb, torch, dev, frames_total=6000):
-    """Poisson arrivals (mean SERVE['rate'] frames/s) from 64 streams, each on a lattice drawn
+def fp32_peak(fb, torch, dev, stream):
+    """Measured FP32 peak: the FFMA and packed FFMA2 probes at full occupancy (8 CTAs of 256
+    threads per SM), each about 12 ms, best of 3 launches, CUDA events on the stream; the SM
+    clock sampled meanwhile."""
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = nsm * 8
+    out = torch.empty(blocks * 256, device=dev)
+    res = {}
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    for packed in (False, True):
+        fb.probe_fp32(packed, 2000, blocks, out, stream)
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = fb.probe_fp32(packed, 200000, blocks, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        res["ffma2_tflops" if packed else "ffma_tflops"] = best
+    time.sleep(0.25)
+    clk = clocks.stop()
+    res["sm_mhz"] = clk.get("sm_mhz")
+    res["source"] = ("FFMA2 (packed fma.rn.f32x2) probe" if res["ffma2_tflops"] > res["ffma_tflops"]
+                     else "FFMA probe") + f", {blocks} CTAs x 256 threads x 8 chains, best of 3"
+    return res
+
+
+def run_serving(fb, torch, dev, frames_total=10000, rate=2000.0):
+    """Poisson arrivals (mean `rate` frames/s) from 64 streams, each on a lattice drawn
     (seeded) from 4x256, 8x64, 16x16; one frame = 384 samples x 16 channels x 2 pols. Frames
     come from a pool of distinct seeded frames in pinned memory; beams land in pinned
     buffers. Returns throughput and latency percentiles of the continuous-batching server."""
@@ -514,7 +652,7 @@ def run_serving(fb, torch, dev, frames_total=6000):
             pool.append(buf)
         pools.append(pool)
     stream_lat = rng.integers(0, len(cfg["lattices"]), cfg["streams"])
-    gaps = rng.exponential(1.0 / cfg["rate"], frames_total)
+    gaps = rng.exponential(1.0 / rate, frames_total)
     streams = rng.integers(0, cfg["streams"], frames_total)
     nout = 4096
     outs = [torch.empty((cfg["nfreq"], p.pad_x, p.pad_y), dtype=torch.float32, pin_memory=True).numpy()
@@ -523,10 +661,12 @@ def run_serving(fb, torch, dev, frames_total=6000):
             for _ in range(nout)]
     samples = 0
     with fb.server_create(plans, cfg["budget"]) as sv:
-        # warm-up: one frame per lattice
+        # warm-up: one frame per lattice (excluded from the statistics below)
         for k in range(len(plans)):
             t = fb.server_submit(sv, k, pools[k][0], ring[k][:outs[k].size].reshape(outs[k].shape))
             fb.server_wait(sv, t, 30.0)
+        st0 = fb.server_stats(sv)
+    with fb.server_create(plans, cfg["budget"]) as sv:
         t0 = time.perf_counter()
         due = t0
         for i in range(frames_total):
@@ -537,33 +677,36 @@ def run_serving(fb, torch, dev, frames_total=6000):
             fb.server_submit(sv, k, pools[k][i % 4], ring[i % nout][:outs[k].size].reshape(outs[k].shape))
             lx, ly = cfg["lattices"][k]
             samples += cfg["n_int"] * cfg["nfreq"] * cfg["npol"] * lx * ly
+        t_sub = time.perf_counter() - t0
         fb.server_wait(sv, -1, 120.0)
         elapsed = time.perf_counter() - t0
         st = fb.server_stats(sv)
     for p in plans:
         p.close()
-    return {"frames": frames_total, "offered_rate_fps": cfg["rate"], "streams": cfg["streams"],
+    return {"frames": frames_total, "offered_rate_fps": rate, "streams": cfg["streams"],
+            "submitted_fps": frames_total / t_sub,
             "achieved_fps": frames_total / elapsed, "antenna_samples_per_s": samples / elapsed,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-            "frames_per_launch": st["frames_per_launch"], "peak_inflight": st["peak_inflight"],
+            "mean_ms": st["mean_ms"], "frames_per_launch": st["frames_per_launch"],
+            "max_frames_per_launch": st["max_frames_per_launch"],
+            "peak_inflight": st["peak_inflight"], "launches": st["launches"],
+            "warmup_server_p50_ms": st0["p50_ms"],
             "hbm_budget_gb": cfg["budget"] / 2 ** 30, "slots": st["slots"],
-            "note": "latency = completion - submission on the host clock, frames submitted at "
-                    "Poisson arrival times; warm-up frames excluded"}
+            "note": "latency = completion - submission on the host clock (taken before the "
+                    "server lock), frames submitted at Poisson arrival times; a fresh server "
+                    "after a warm-up server"}
 
 
-def run_batched(args):
-    """Twelve arrays drawn (seed 4) from the six lattice shapes, 64-512 channels each, 8192
-    samples, 2 pols, n_int 256, half-sine weights; one fftbf_batch_execute per step."""
-    import torch
+BATCH_T, BATCH_NINT, BATCH_TBLK = 8192, 256, 256
+
+
+def batched_setup(torch, dev, T):
+    """The batched workload: twelve arrays drawn (seed 4) from the six lattice shapes, 64-512
+    channels each, T samples, 2 pols, n_int 256, half-sine weights; device voltages are
+    copies of a seeded 256-sample block per array."""
     import paper_1710_08591_gb300 as fb
-    fb.build()
     rng = np.random.default_rng(4)
-    dev = torch.device("cuda", 0)
-    T, n_int, npol, t_blk = 8192, 256, 2, 256
-    if args.profile_case:
-        # small case for ncu: 512 samples (about 2.6 GB of voltages), many launches so that
-        # one of the run's own launches follows the tuner's (at most ~110 launches)
-        T = 512
+    npol = 2
     picks = rng.integers(0, len(synth.BATCH_LATTICES), 12)
     nfs = rng.integers(64, 513, 12)
     plans, dvs, outs, samples, flops = [], [], [], 0, 0.0
@@ -571,64 +714,98 @@ def run_batched(args):
         lx, ly = synth.BATCH_LATTICES[li]
         lmx, lmy = lx, 2 * synth.next_pow2(ly)
         wts = synth.separable_weights(synth.half_sine(lx), synth.half_sine(ly))
-        plans.append(fb.plan_create(lx, ly, lmx, lmy, npol, int(nf), n_int, weights=wts))
-        blk = synth.volts(t_blk, int(nf), npol, lx, ly, seed=400 + i,
+        plans.append(fb.plan_create(lx, ly, lmx, lmy, npol, int(nf), BATCH_NINT, weights=wts))
+        blk = synth.volts(BATCH_TBLK, int(nf), npol, lx, ly, seed=400 + i,
                           sources=synth.seeded_sources(410 + i, 2, 1.5))
         hb = torch.from_numpy(blk.reshape(-1))
-        dv = torch.empty(hb.numel() * (T // t_blk), dtype=torch.uint8, device=dev)
-        for c in range(T // t_blk):
+        dv = torch.empty(hb.numel() * (T // BATCH_TBLK), dtype=torch.uint8, device=dev)
+        for c in range(T // BATCH_TBLK):
             dv[c * hb.numel():(c + 1) * hb.numel()].copy_(hb)
         dvs.append(dv)
-        outs.append(torch.empty((T // n_int, int(nf), lmx, lmy), device=dev))
+        outs.append(torch.empty((T // BATCH_NINT, int(nf), lmx, lmy), device=dev))
         samples += T * int(nf) * npol * lx * ly
         flops += T * int(nf) * npol * flops_per_snapshot(lx, ly, lmx, lmy)
+    arrays = [[int(synth.BATCH_LATTICES[li][0]), int(synth.BATCH_LATTICES[li][1]), int(nf)]
+              for li, nf in zip(picks, nfs)]
+    return plans, dvs, outs, samples, flops, arrays
+
+
+def batched_form(fb, torch, dev, steps, warmup, fp32_pk):
+    """Time the batched configuration: one fftbf_batch_execute (one persistent launch,
+    CUDA-graph replay) per step, CUDA events on its stream."""
+    T = BATCH_T
+    plans, dvs, outs, samples, flops, arrays = batched_setup(torch, dev, T)
     stream = torch.cuda.Stream(dev)
     with fb.batch_create(plans) as b, torch.cuda.stream(stream):
         tiles = [fb.batch_tuned_steps(b, i) for i in range(len(plans))]
-        for _ in range(args.warmup):
+        grid = fb.batch_grid(b)
+        for _ in range(warmup):
             fb.batch_execute(b, dvs, T, outs, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fb.batch_execute(b, dvs, T, outs, stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / args.steps
-        if args.profile_case:
-            for _ in range(200):
-                fb.batch_execute(b, dvs, T, outs, stream)
-            torch.cuda.synchronize(dev)
-            print("profile case done", flush=True)
-            for p in plans:
-                p.close()
-            return 0
+        ms = e0.elapsed_time(e1) / steps
     byts = sum(d.numel() for d in dvs) + sum(o.numel() * 4 for o in outs)
+    items = sum(o.shape[0] * o.shape[1] for o in outs)
     peaks, src = measured_peaks()
-    line = {"metric": "antenna-samples/s, batched uneven lattices", "value": samples / (ms / 1e3),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "12 arrays from {4x256, 8x64, 16x16, 2x512, 1x1024, 3x128} "
-                                   "(seed 4), 64-512 channels, 8192 samples, 2 pols, N-S padded "
-                                   "to 2x next pow2, n_int 256, half-sine weights",
-                       "arrays": [[int(synth.BATCH_LATTICES[li][0]), int(synth.BATCH_LATTICES[li][1]), int(nf)]
-                                  for li, nf in zip(picks, nfs)],
-                       "tuned_snapshots_per_step": tiles,
-                       "launch": "one persistent kernel per step (CUDA graph replay)",
-                       "l2": "inputs larger than L2"},
-            "gpu_launches": args.steps,
+    for p in plans:
+        p.close()
+    del dvs, outs
+    torch.cuda.empty_cache()
+    return {"metric": "antenna-samples/s, batched uneven lattices", "value": samples / (ms / 1e3),
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "workload": "12 arrays from {4x256, 8x64, 16x16, 2x512, 1x1024, 3x128} (seed 4), "
+                        "64-512 channels, 8192 samples, 2 pols, N-S padded to 2x next pow2, "
+                        "n_int 256, half-sine weights",
+            "arrays": arrays, "tuned_snapshots_per_step": tiles, "items": items, "grid": grid,
+            "launch": "one persistent kernel per step (CUDA graph replay)",
+            "l2": "inputs larger than L2",
             "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": flops / (ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak": fp32_pk, "unit": "TFLOP/s",
+                         "frac": flops / (ms / 1e3) / 1e12 / fp32_pk,
                          "traffic": TRAFFIC_BATCH, "kernel": "batch_kernel",
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "peak_source": "measured FP32 probe",
                          "hbm": {"achieved_gbs": byts / (ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
                                  "frac": byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
                                  "peak_source": src}}}
+
+
+def run_batched(args):
+    """The batched configuration alone (--workload batched), or its small ncu case."""
+    import torch
+    import paper_1710_08591_gb300 as fb
+    fb.build()
+    dev = torch.device("cuda", 0)
+    if args.profile_case:
+        # small case for ncu: 512 samples (about 2.6 GB of voltages), many launches so that
+        # one of the run's own launches follows the tuner's (at most ~110 launches)
+        T = 512
+        plans, dvs, outs, _, _, _ = batched_setup(torch, dev, T)
+        stream = torch.cuda.Stream(dev)
+        with fb.batch_create(plans) as b, torch.cuda.stream(stream):
+            for _ in range(200):
+                fb.batch_execute(b, dvs, T, outs, stream)
+            torch.cuda.synchronize(dev)
+        print("profile case done", flush=True)
+        for p in plans:
+            p.close()
+        return 0
+    stream = torch.cuda.current_stream(dev)
+    fp32 = fp32_peak(fb, torch, dev, stream)
+    r = batched_form(fb, torch, dev, args.steps, args.warmup,
+                     max(fp32["ffma_tflops"], fp32["ffma2_tflops"]))
+    line = {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "arrays", "tuned_snapshots_per_step",
+                                         "items", "grid", "launch", "l2")},
+            "gpu_launches": args.steps, "roofline": r["roofline"], "fp32_probe": fp32}
     print(json.dumps(line), flush=True)
-    for p in plans:
-        p.close()
     return 0
 
 
@@ -704,7 +881,7 @@ def main():
     ap.add_argument("--workload", choices=["chime", "batched"], default="chime")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-frames", type=int, default=6000)
+    ap.add_argument("--serve-frames", type=int, default=10000)
     ap.add_argument("--profile-case", action="store_true",
                     help="run a small case of the timed kernels (for ncu) and exit")
     ap.add_argument("--tied", action="store_true",

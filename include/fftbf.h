@@ -231,6 +231,9 @@ int fftbf_batch_execute(fftbf_batch* batch, const uint8_t* const* volts_dev, int
                         float* const* beams_dev, void* stream);
 /* Snapshots per step the autotuner chose for plan i of the batch (>= 1), or < 0. */
 int fftbf_batch_tuned_steps(const fftbf_batch* batch, int i);
+/* CTAs of each batched launch: the launch's persistent grid (SMs x resident CTAs per SM);
+ * work items beyond it are taken from the device queue in turn. */
+int fftbf_batch_grid(const fftbf_batch* batch);
 /* Free the batch (waits for its last launch). NULL is a no-op. */
 void fftbf_batch_destroy(fftbf_batch* batch);
 
@@ -253,16 +256,27 @@ typedef struct {
   int64_t launches;              /* batched launches issued */
   int64_t peak_inflight;         /* most frames holding device slots at once */
   int64_t slots;                 /* device slots the budget allows */
+  int64_t max_frames_per_launch; /* largest number of frames in one launch */
+  int64_t max_items_per_launch;  /* largest number of (frame, channel) items in one launch */
+  int64_t grid;                  /* CTAs of every launch (items beyond it are taken in turn) */
   double frames_per_launch;      /* mean frames per launch */
-  double p50_ms, p99_ms, max_ms, mean_ms;  /* completion - submission, host clock */
+  double p50_ms, p99_ms, max_ms, mean_ms;  /* completion - submission, host clock; the
+                                              percentiles come from a uniform sample of at
+                                              most 65536 frames (exact up to that count) */
 } fftbf_server_stats_t;
 /* n lattice plans (1..64, FP32 precision); starts the scheduler thread. NULL on error. */
 fftbf_server* fftbf_server_create(fftbf_plan* const* lattices, int n, int64_t hbm_budget_bytes);
-/* Queue one frame of lattice `lattice`; returns its ticket (>= 0) or a negative error. */
+/* Queue one frame of lattice `lattice`; returns its ticket (>= 0) or a negative error.
+ * The frame's latency clock starts on entry, before the call waits for the server lock. */
 int64_t fftbf_server_submit(fftbf_server* server, int lattice, const uint8_t* frame_host,
                             float* beams_host);
+/* hold != 0: admit and stage frames but start no launch until called again with 0 (then
+ * every staged frame, up to 64 per launch, goes out at once). Lets a caller gather a burst
+ * into one launch; fftbf_server_destroy releases a hold. FFTBF_OK or FFTBF_EINVAL. */
+int fftbf_server_hold(fftbf_server* server, int hold);
 /* Wait until frame `ticket` (or, with ticket < 0, every submitted frame) has completed:
- * FFTBF_OK, FFTBF_ETIMEOUT after timeout_s seconds, or the server's CUDA error. */
+ * FFTBF_OK, FFTBF_ETIMEOUT after timeout_s seconds, FFTBF_EINVAL for a ticket never
+ * issued, or the server's CUDA error. */
 int fftbf_server_wait(fftbf_server* server, int64_t ticket, double timeout_s);
 /* Counters and latency percentiles so far; returns the server's error state. */
 int fftbf_server_stats(fftbf_server* server, fftbf_server_stats_t* out);
@@ -299,6 +313,16 @@ int fftbf_debug_tc_gemm(const uint16_t* a_dev, const uint16_t* b_dev, int n, int
                         int padded, float* d_dev, void* stream);
 
 /*
+ * FP32 throughput probe (measurement, not part of the method): `blocks` CTAs of 256
+ * threads each run 8 independent multiply-add chains for `iters` steps, as scalar FFMA
+ * (packed = 0) or as the packed two-lane FFMA2 (packed = 1, fma.rn.f32x2). out_dev:
+ * device float [blocks * 256], overwritten. *flops_out receives the flops the launch
+ * performs (2 per FMA); the caller times the launch on `stream` (asynchronous).
+ */
+int fftbf_probe_fp32(int packed, int64_t iters, int blocks, float* out_dev, double* flops_out,
+                     void* stream);
+
+/*
  * Test hook for failure detection without a GPU fault: a kernel waits, with the same
  * bounded wait the tensor-core kernels use, on an mbarrier that nothing arrives on. The
  * wait gives up after limit_us microseconds of device time (1..2000000) and the call
@@ -326,6 +350,9 @@ int fftbf_debug_wait_timeout(int limit_us, void* stream);
  *   volts_dev, T, beams_dev, stream  as for fftbf_execute.
  * The first call on a device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream capture begins.
+ * The address is kept for the life of the process: after cudaDeviceReset on a device,
+ * the next call on that device would use the old context's address, so a caller that
+ * resets a device must not call this entry point on it again.
  * Every call rewrites the tables before its transform reads them, so nothing carries
  * over from the previous call. All calls share the one array: calls whose work
  * overlaps on the GPU (on different streams, or from several host threads) race on it

@@ -21,9 +21,9 @@ import numpy as np
 __all__ = ["lib", "build", "FFTBF_OK", "PREC_FP32", "PREC_TC_FP16", "PREC_TC_BF16", "PREC_TC_FP16X3",
            "FftbfError", "Plan", "plan_create", "plan_set_precision", "execute", "execute_host", "tied_beams", "tied_set_window", "stacked_shape",
            "stacked_visibilities", "localise",
-           "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "Batch", "batch_create",
-           "batch_execute", "batch_tuned_steps", "batch_destroy", "Server", "server_create",
-           "server_submit", "server_wait", "server_stats", "server_destroy"]
+           "plan_sync", "destroy", "last_error", "last_error_code", "debug_unpack", "execute_noalloc", "debug_tc_gemm", "debug_wait_timeout", "probe_fp32", "Batch", "batch_create",
+           "batch_execute", "batch_tuned_steps", "batch_grid", "batch_destroy", "Server", "server_create",
+           "server_submit", "server_hold", "server_wait", "server_stats", "server_destroy"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfftbf.so")
@@ -92,12 +92,18 @@ def lib() -> ctypes.CDLL:
             L.fftbf_batch_execute.argtypes = [vp, vp, c_i64, vp, vp]
             L.fftbf_batch_tuned_steps.restype = c_int
             L.fftbf_batch_tuned_steps.argtypes = [vp, c_int]
+            L.fftbf_probe_fp32.restype = c_int
+            L.fftbf_probe_fp32.argtypes = [c_int, c_i64, c_int, vp, vp, vp]
+            L.fftbf_batch_grid.restype = c_int
+            L.fftbf_batch_grid.argtypes = [vp]
             L.fftbf_batch_destroy.restype = None
             L.fftbf_batch_destroy.argtypes = [vp]
             L.fftbf_server_create.restype = vp
             L.fftbf_server_create.argtypes = [vp, c_int, c_i64]
             L.fftbf_server_submit.restype = c_i64
             L.fftbf_server_submit.argtypes = [vp, c_int, vp, vp]
+            L.fftbf_server_hold.restype = c_int
+            L.fftbf_server_hold.argtypes = [vp, c_int]
             L.fftbf_server_wait.restype = c_int
             L.fftbf_server_wait.argtypes = [vp, c_i64, ctypes.c_double]
             L.fftbf_server_stats.restype = c_int
@@ -323,6 +329,11 @@ def batch_tuned_steps(batch: Batch, i: int) -> int:
     return r
 
 
+def batch_grid(batch: Batch) -> int:
+    """CTAs of each batched launch (work items beyond it are taken from the queue in turn)."""
+    return int(lib().fftbf_batch_grid(batch.handle))
+
+
 def batch_destroy(batch: Batch) -> None:
     batch.close()
 
@@ -330,7 +341,9 @@ def batch_destroy(batch: Batch) -> None:
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("peak_inflight", ctypes.c_int64),
-                ("slots", ctypes.c_int64), ("frames_per_launch", ctypes.c_double),
+                ("slots", ctypes.c_int64), ("max_frames_per_launch", ctypes.c_int64),
+                ("max_items_per_launch", ctypes.c_int64), ("grid", ctypes.c_int64),
+                ("frames_per_launch", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
 
@@ -386,6 +399,11 @@ def server_submit(server: Server, lattice: int, frame: np.ndarray, beams: np.nda
     return int(t)
 
 
+def server_hold(server: Server, hold: bool) -> None:
+    """Stage frames without launching while `hold` is true; releasing launches them together."""
+    _check(lib().fftbf_server_hold(server.handle, 1 if hold else 0))
+
+
 def server_wait(server: Server, ticket: int = -1, timeout_s: float = 60.0) -> None:
     _check(lib().fftbf_server_wait(server.handle, int(ticket), float(timeout_s)))
     if ticket >= 0:
@@ -418,6 +436,15 @@ def execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, weights, volts, T:
     memory); weights is a device tensor of nx*ny complex64 values or None."""
     _check(lib().fftbf_execute_noalloc(nx, ny, pad_x, pad_y, npol, nfreq, n_int, _dptr(weights),
                                        _dptr(volts), int(T), _dptr(beams), _stream(stream)))
+
+
+def probe_fp32(packed: bool, iters: int, blocks: int, out, stream=None) -> float:
+    """Launch the FP32 throughput probe (scalar FFMA or packed FFMA2) on `stream`; returns
+    the flops the launch performs. `out`: device float tensor of blocks * 256 elements."""
+    fl = ctypes.c_double(0.0)
+    _check(lib().fftbf_probe_fp32(1 if packed else 0, int(iters), int(blocks), _dptr(out),
+                                  ctypes.byref(fl), _stream(stream)))
+    return fl.value
 
 
 def debug_wait_timeout(limit_us: int, stream=None) -> int:

@@ -27,6 +27,11 @@ int set_error(int code, const char* fmt, ...) {
   return code;
 }
 
+void clear_error() {
+  g_error.clear();
+  g_error_code = FFTBF_OK;
+}
+
 int cuda_error(cudaError_t e, const char* what) {
   const int code = (e == cudaErrorMemoryAllocation) ? FFTBF_ENOMEM : FFTBF_ECUDA;
   return set_error(code, "%s: %s", what, cudaGetErrorString(e));

@@ -24,6 +24,8 @@ struct NvtxRange {
 // Thread-local error message plus status code.
 int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what);
+// Forget the calling thread's last error (after a recovered failure, e.g. a fallback).
+void clear_error();
 
 #define FFTBF_CUDA_TRY(call)                               \
   do {                                                     \

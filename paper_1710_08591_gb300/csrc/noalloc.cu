@@ -95,6 +95,7 @@ extern "C" int fftbf_execute_noalloc(int nx, int ny, int pad_x, int pad_y, int n
   a.nyf = ny < pad_y ? ny : pad_y;
   a.nwin = T / n_int;
   a.ew_dft = (pad_x == nx) && (pad_x & (pad_x - 1)) == 0 && pad_x <= 16;
+  a.real_w = weights_dev ? 0 : 1;      // the unit weights written above are real
   const int nsnap = n_int * npol;
   int S = kMaxElems / (pad_x * pad_y);
   if (S < 1) S = 1;

@@ -629,8 +629,15 @@ int tied_prepare(TiedTables& tt, int nx, int ny, int mx, int my, int nfreq, int 
     tt.tc = 0;
     if (tied_tc_eligible(dense_x, mx, my)) {
       tt.tc_n_tied = n_tied;
-      // without room for the split tables the CUDA-core GEMM serves (its tables are built)
-      if (tied_tc_build(tt, (int64_t)nuv, mx, my, st) != FFTBF_OK) tt.tc = 0;
+      // without room for the split tables the CUDA-core GEMM serves (its tables are
+      // built); any other failure is the call's error
+      const int trc = tied_tc_build(tt, (int64_t)nuv, mx, my, st);
+      if (trc == FFTBF_ENOMEM) {
+        tt.tc = 0;
+        clear_error();
+      } else if (trc != FFTBF_OK) {
+        return trc;
+      }
     }
   }
   tt.built_version = tt.version;
@@ -643,7 +650,8 @@ int tied_launch(TiedTables& tt, const float* beams, int64_t nwin, int nfreq, int
   if (nwin <= 0) return FFTBF_OK;
   if (tt.tc && tt.kx == 0) {
     const int rc = tied_tc_launch(tt, beams, nwin, nfreq, mx, my, out, st);
-    if (rc != FFTBF_ENOMEM) return rc;           // no room for the beam split: CUDA-core GEMM
+    if (rc != FFTBF_ENOMEM) return rc;
+    clear_error();                               // no room for the beam split: CUDA-core GEMM
   }
   if (tt.kx > 0 && tt.ky > 0) {
     dim3 grid((tt.n_tied + 255) / 256, (unsigned)std::min(nfreq, 65535),

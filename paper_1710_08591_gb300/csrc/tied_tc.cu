@@ -292,6 +292,10 @@ int tied_tc_build(TiedTables& tt, int64_t nuv, int mx, int my, cudaStream_t st) 
   const int nfreq = (int)(nuv / n_tied);
   const int64_t nts = (n_tied + ttc::TM - 1) / ttc::TM;
   const size_t halves = (size_t)nfreq * nts * ttc::TM * my;      // padded to whole tiles
+  // test hook: FFTBF_TEST_TIED_TC_NOMEM=1 makes the split tables look unallocatable, so
+  // that the fallback to the CUDA-core GEMM can be exercised without exhausting the device
+  const char* nomem = getenv("FFTBF_TEST_TIED_TC_NOMEM");
+  if (nomem && nomem[0] == '1') return set_error(FFTBF_ENOMEM, "split tied-beam tables (test hook)");
   bool ok = cudaMalloc(&tt.wyh, halves * sizeof(__half)) == cudaSuccess &&
             cudaMalloc(&tt.wyl, halves * sizeof(__half)) == cudaSuccess &&
             cudaMalloc(&tt.wye, nuv * sizeof(int)) == cudaSuccess &&

@@ -39,3 +39,16 @@ def rel_err_of_mean(got, ref):
     ref = np.asarray(ref, dtype=np.float64)
     mean = ref.mean(axis=(-2, -1), keepdims=True)
     return np.abs(got - ref) / np.where(mean > 0, mean, 1.0)
+
+
+def parseval_totals(v, w, n_int, mx, my):
+    """Total power of every (window, channel) over the full padded grid by Parseval:
+    mx * my * sum_{t in window, p, ix, iy} |w x|^2 (valid when mx >= nx and my >= ny, so
+    nothing folds). v: uint8 [T][F][P][nx][ny]; w: complex [nx][ny] or None (all ones).
+    |x|^2 per byte value comes from the oracle's unpack."""
+    v = np.asarray(v)
+    T, F, P, nx, ny = v.shape
+    lut = np.abs(oracle.unpack(np.arange(256, dtype=np.uint8))) ** 2
+    w2 = np.ones((nx, ny)) if w is None else np.abs(np.asarray(w, dtype=np.complex128)) ** 2
+    e = lut[v].reshape(T // n_int, n_int, F, P, nx, ny).sum(axis=(1, 3))   # [J][F][nx][ny]
+    return mx * my * np.einsum("jfab,ab->jf", e, w2)

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import TOL_BEAM, make_case, oracle_beams
+from helpers import TOL_BEAM, make_case, oracle_beams, parseval_totals
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -112,6 +112,42 @@ def test_batch_constant_size_and_runtime_instances_bit_identical():
     for k, (x, y) in enumerate(zip(*res)):
         assert np.all(np.isfinite(x)), arrs[k]["shape"]
         assert np.array_equal(x, y), arrs[k]["shape"]
+
+
+def test_batch_every_cta_takes_several_items():
+    """Items outnumber the launch grid several times over, so every CTA takes items from
+    the queue again and again, as in the bench: sampled (window, channel) slices of every
+    array against the oracle, every item against Parseval, and one array alone
+    bit-identical to its place in the mix."""
+    T, n_int, nf = 64, 16, 160
+    arrs = _arrays([nf] * 6, T, n_int, seed=120)
+    plans = [fb.plan_create(*a["shape"], weights=a["w"]) for a in arrs]
+    dvs = [torch.from_numpy(a["v"].reshape(-1)).cuda() for a in arrs]
+    outs = [torch.full((T // n_int, nf, a["shape"][2], a["shape"][3]), float("nan"),
+                       device="cuda") for a in arrs]
+    with fb.batch_create(plans) as b:
+        grid = fb.batch_grid(b)
+        items = sum(o.shape[0] * o.shape[1] for o in outs)
+        assert items >= 3 * grid, (items, grid)
+        fb.batch_execute(b, dvs, T, outs, None)
+        torch.cuda.synchronize()
+    got = [o.cpu().numpy() for o in outs]
+    rng = np.random.default_rng(3)
+    for a, g in zip(arrs, got):
+        nx, ny, mx, my, npol, _, _ = a["shape"]
+        assert np.all(np.isfinite(g)), a["shape"]
+        tot = parseval_totals(a["v"], a["w"], n_int, mx, my)
+        prel = np.abs(g.astype(np.float64).sum(axis=(-2, -1)) - tot) / tot
+        assert prel.max() <= 1e-6, (a["shape"], prel.max())
+        for j, f in [(0, 0), (T // n_int - 1, nf - 1)] + [tuple(rng.integers(0, (T // n_int, nf)))]:
+            v = np.ascontiguousarray(a["v"][j * n_int:(j + 1) * n_int, f:f + 1])
+            ref = oracle_beams(v, a["w"], nx, ny, mx, my, npol, 1, n_int)[0, 0]
+            err = np.abs(g[j, f] - ref) / ref
+            assert err.max() <= TOL_BEAM, (a["shape"], j, f, err.max())
+    alone, _ = _run([arrs[2]], T)
+    assert np.array_equal(alone[0], got[2])
+    for p_ in plans:
+        p_.close()
 
 
 def test_batch_rejects_unsupported_shape():

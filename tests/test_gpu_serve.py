@@ -51,18 +51,24 @@ def test_frames_same_alone_and_in_mix(setup):
                 t = fb.server_submit(sv, k, frames[k][j], out)
                 fb.server_wait(sv, t, 60.0)
                 alone[(k, j)] = out
-    # mix: everything submitted at once, interleaved across lattices, twice over
+    # mix: everything submitted while the server is held, interleaved across lattices,
+    # twice over, then released: the frames go out together
     mixed = {}
     with fb.server_create(plans, budget) as sv:
+        fb.server_hold(sv, True)
         for rep in range(2):
             for j in range(3):
                 for k in range(len(plans)):
                     out = _out(plans[k])
                     fb.server_submit(sv, k, frames[k][j], out)
                     mixed[(k, j, rep)] = out
+        fb.server_hold(sv, False)
         fb.server_wait(sv, -1, 120.0)
         st = fb.server_stats(sv)
     assert st["completed"] == st["submitted"] == 18
+    # a mix happened: frames of all three lattices shared launches and were in flight together
+    assert st["max_frames_per_launch"] > 1 and st["frames_per_launch"] > 1, st
+    assert st["launches"] < st["submitted"] and st["peak_inflight"] > 1, st
     assert st["p99_ms"] >= st["p50_ms"] > 0.0
     for (k, j, rep), out in mixed.items():
         assert np.array_equal(out, alone[(k, j)]), (k, j, rep)
@@ -98,3 +104,46 @@ def test_bad_lattice_index_rejected(setup):
         with pytest.raises(fb.FftbfError) as e:
             fb.server_submit(sv, 7, frames[0][0], _out(plans[0]))
         assert e.value.code == -1
+
+
+def test_burst_beyond_the_grid_same_as_alone():
+    """A held burst of 63 frames of 16 channels each (1008 work items in one launch, more
+    than the launch's CTAs, so CTAs take several items from the queue): every frame's
+    beams are bit-identical to the same frame served alone."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fb.build()
+    nf, nint = 16, 32
+    plans, frames = [], []
+    for k, (nx, ny) in enumerate(SERVE_LATTICES):
+        w = synth.separable_weights(synth.half_sine(nx), synth.half_sine(ny))
+        plans.append(fb.plan_create(nx, ny, nx, 2 * synth.next_pow2(ny), NPOL, nf, nint, weights=w))
+        frames.append([synth.volts(nint, nf, NPOL, nx, ny, seed=700 + 10 * k + j,
+                                   sources=synth.seeded_sources(800 + k + j, 2, 1.5))
+                       for j in range(3)])
+    try:
+        alone = {}
+        with fb.server_create(plans, 1 << 30) as sv:
+            for k in range(3):
+                for j in range(3):
+                    out = _out(plans[k])
+                    fb.server_wait(sv, fb.server_submit(sv, k, frames[k][j], out), 60.0)
+                    alone[(k, j)] = out
+        burst = []
+        with fb.server_create(plans, 1 << 30) as sv:
+            fb.server_hold(sv, True)
+            for i in range(63):
+                k, j = i % 3, (i // 3) % 3
+                out = _out(plans[k])
+                fb.server_submit(sv, k, frames[k][j], out)
+                burst.append((k, j, out))
+            fb.server_hold(sv, False)
+            fb.server_wait(sv, -1, 120.0)
+            st = fb.server_stats(sv)
+        assert st["max_frames_per_launch"] == 63 and st["launches"] == 1, st
+        assert st["max_items_per_launch"] == 63 * nf > st["grid"], st
+        for k, j, out in burst:
+            assert np.array_equal(out, alone[(k, j)]), (k, j)
+    finally:
+        for p in plans:
+            p.close()

@@ -63,3 +63,30 @@ def test_tied_tensor_core_matches_oracle_and_cuda_cores(shape, n_tied, monkeypat
     monkeypatch.setenv("FFTBF_TIED_TC", "0")                 # the CUDA-core GEMM
     simt = _tied(P, shape, w, u, v, n_tied)
     assert (np.abs(got - simt) / scale).max() <= TOL_BEAM
+
+
+def test_tied_falls_back_to_cuda_cores_when_split_tables_do_not_fit(monkeypatch):
+    """With the split tables unallocatable (a test hook makes tied_tc_build report
+    FFTBF_ENOMEM without touching the allocator), the call succeeds on the CUDA-core GEMM,
+    matches the oracle's regridding and leaves no error behind on the thread."""
+    shape = (4, 256, 4, 512, 1, 2, 256, 8)
+    nx, ny, mx, my, npol, nfreq, T, n_int = shape
+    v8, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="random", seed=44)
+    nwin, n_tied = T // n_int, 130
+    P = torch.empty((nwin, nfreq, mx, my), device="cuda")
+    with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
+        fb.execute(plan, torch.from_numpy(v8.reshape(-1)).cuda(), T, P)
+        fb.plan_sync(plan)
+    rng = np.random.default_rng(12)
+    u = rng.integers(0, mx, (nfreq, n_tied)) / mx
+    v = rng.random((nfreq, n_tied))
+    monkeypatch.setenv("FFTBF_TEST_TIED_TC_NOMEM", "1")
+    got = _tied(P, shape, w, u, v, n_tied)
+    assert fb.last_error_code() == 0 and fb.last_error() == ""
+    Pn = P.cpu().numpy().astype(np.float64)
+    scale = _scale(Pn, u, v, nx, ny)
+    assert np.all(np.isfinite(got))
+    assert (np.abs(got - oracle.tied_regrid(Pn, u, v, nx, ny)) / scale).max() <= TOL_BEAM
+    monkeypatch.setenv("FFTBF_TIED_TC", "0")
+    simt = _tied(P, shape, w, u, v, n_tied)
+    assert np.array_equal(got, simt)                         # the same CUDA-core kernel ran
