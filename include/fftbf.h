@@ -304,7 +304,9 @@ int fftbf_debug_unpack(const uint8_t* in_dev, int64_t n, float* out_dev, void* s
 /*
  * Test hook for the tensor-core building blocks: D[128][n] = A[128][32] B[n][32]^T with
  * 16-bit operands (FP16, or BF16 if bf16 != 0), staged in the kernels' shared-memory
- * layouts (A with the padded strides of the stage-2 operand if padded != 0), one pair of
+ * layouts: `padded` = 0 canonical K-major A, 1 K-major A with the padded strides of the
+ * stage-2 operand, 2 MN-major A (element (m, k) at byte (m%8)*2 + (k%8)*16 + (m/8)*128 +
+ * (k/8)*2048, the operand layout of the warp-specialised FP16 kernel); one pair of
  * tcgen05.mma instructions, FP32 accumulation in tensor memory. n = 32, 64, 128 or 256.
  * Device pointers, row-major. Synchronises `stream`; FFTBF_ETIMEOUT if the tensor core
  * did not complete within one second.

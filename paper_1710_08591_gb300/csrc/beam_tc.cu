@@ -868,9 +868,19 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const BeamArgs& a = ta.b;
   if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
-  // The serial kernel (several CTAs per SM, every warp in every phase) measures faster than
-  // the warp-specialised pipeline on the 4x256 lattice; FFTBF_TC_PIPE=1 selects the latter.
+  // FP16 on the 4x256 lattice: the warp-specialised kernel with MN-major planar operands
+  // (beam_tcw.cu) unless FFTBF_TC_KERNEL=serial or FFTBF_TC_PIPE=1 ask for the kernels
+  // below. Of those two, the serial kernel (several CTAs per SM, every warp in every phase)
+  // measures faster than the first warp-specialised pipeline on the 4x256 lattice.
   const char* pipe = getenv("FFTBF_TC_PIPE");
+  const char* which = getenv("FFTBF_TC_KERNEL");
+  const bool old_kernel = (pipe && pipe[0] && pipe[0] != '0') || (which && which[0] == 's');
+  if (!old_kernel && tcw_eligible(ta)) {
+    TcArgs tw = ta;
+    tw.b1 = ta.b1w;
+    tw.b2 = ta.b2w;
+    return launch_beams_tcw(tw, nsm, st);
+  }
   if (ta.split || !(pipe && pipe[0] && pipe[0] != '0')) {   // the split form is serial only
     const TcSmem L = tc_smem_layout(a.nx * a.ny, ta.split != 0, ta.w4 != 0);
     // at most 8 CTAs of 64 TMEM columns per SM: keep a ninth from fitting (registers and
@@ -977,9 +987,13 @@ __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A
                                                                 int n, int padded, float* D, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
-  const int albo = padded ? tcl::A2_LBO : tcl::A1_LBO, asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
+  // padded: 0 canonical K-major A, 1 K-major with the stage-2 operand's padded strides,
+  // 2 MN-major A (element (m, k) at (m%8)*2 + (k%8)*16 + (m/8)*128 + (k/8)*2048)
+  const bool mn = padded == 2;
+  const int albo = mn ? 2048 : (padded ? tcl::A2_LBO : tcl::A1_LBO);
+  const int asbo = mn ? 128 : (padded ? tcl::A2_SBO : tcl::A1_SBO);
   unsigned char* as = smem;
-  unsigned char* bs = smem + 16 * asbo;
+  unsigned char* bs = smem + (mn ? 8192 : 16 * asbo);
   uint64_t* bar = reinterpret_cast<uint64_t*>(bs + (n / 8) * tcl::B_SBO);
   uint32_t* taddr_sm = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -991,7 +1005,15 @@ __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A
     tc::mbar_init(bar, 1);
     tc::mbar_init_fence();
   }
-  load_kmajor(as, A, 128, albo, asbo, tid, 128);
+  if (mn) {
+    for (int i = tid; i < 128 * 32; i += 128) {
+      const int m = i >> 5, k = i & 31;
+      *reinterpret_cast<uint16_t*>(as + (m & 7) * 2 + (k & 7) * 16 + (m >> 3) * asbo + (k >> 3) * albo) =
+          A[m * 32 + k];
+    }
+  } else {
+    load_kmajor(as, A, 128, albo, asbo, tid, 128);
+  }
   load_kmajor(bs, B, n, tcl::B_LBO, tcl::B_SBO, tid, 128);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -999,7 +1021,7 @@ __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A
   tc::fence_after_sync();
   const uint32_t tbase = *taddr_sm;
   if (tid == 0) {
-    const uint32_t id = tc::idesc_f16(128, n, BF16);
+    const uint32_t id = tc::idesc_f16(128, n, BF16) | (mn ? (1u << 15) : 0u);   // A MN-major
     for (int kk = 0; kk < 2; ++kk)
       tc::mma_f16(tbase, tc::smem_desc(tc::smem_u32(as) + kk * 2 * albo, albo, asbo),
                   tc::smem_desc(tc::smem_u32(bs) + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO),
@@ -1042,13 +1064,14 @@ int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st) {
   return FFTBF_OK;
 }
 
-int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
+int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, int layout,
                          float* D, int* err, cudaStream_t st) {
+  const bool padded = layout == 1;
   const int asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
-  const size_t smem = 16 * asbo + (n / 8) * tcl::B_SBO + 64;
+  const size_t smem = (layout == 2 ? 8192 : 16 * asbo) + (n / 8) * tcl::B_SBO + 64;
   auto kern = bf16 ? debug_tc_gemm_kernel<true> : debug_tc_gemm_kernel<false>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<1, 128, smem, st>>>(A, B, n, padded ? 1 : 0, D, err);
+  kern<<<1, 128, smem, st>>>(A, B, n, layout, D, err);
   FFTBF_CUDA_TRY(cudaGetLastError());
   return FFTBF_OK;
 }

@@ -1,0 +1,525 @@
+// Tensor-core FP16 form of the FFT-beam hot path on the 4x256 lattice (4 E-W beams x 512
+// N-S beams, Eq. fftbeamform with the N-S axis zero-padded to 2n, Eq. b2n-1), as a
+// warp-specialised pipeline.
+//
+// The 512-point N-S transform of each (snapshot, E-W beam) is split as 512 = 32 x 16
+// (n = n2 + 16 n1, k = k1 + 32 k2; inputs with n1 >= 16 are the padding):
+//   stage 1 (tcgen05.mma, M=128 N=64 K=32): rows (snapshot s, E-W beam A, n2) of a snapshot
+//     pair, the pruned 32-point DFT over n1 as a real-embedded GEMM;
+//   twiddle: X1 *= W512^(n2 k1) while draining TMEM, in packed half arithmetic;
+//   stage 2 (tcgen05.mma, M=128 N=32 K=32 per snapshot): rows (A, k1), a 16-point DFT over
+//     n2 giving X[k1 + 32 k2]; the thread owning TMEM row (A, k1) squares it and integrates
+//     over time and polarisation in registers (Eq. bf).
+// Both GEMM A operands are stored MN-major (rows contiguous for each K element) with complex
+// values planar along K (real parts at K 0..15, imaginary parts at K 16..31), so that:
+//   * the input stage packs two adjacent N-S feeds (adjacent rows n2) into one half2 and
+//     writes 8 bytes per (E-W beam, component);
+//   * the stage-1 drain packs two adjacent k1 (adjacent stage-2 rows) into one half2 and
+//     writes 16 bytes per (component, 8 k1) instead of one 4-byte value per k1.
+// The B operands (DFT matrices) stay K-major. Stage-1 outputs are planar along N (real
+// parts of k1 0..31, then imaginary parts), stage-2 outputs interleaved (re, im) per k2, so
+// that the detector squares both parts of a beam with one packed FFMA2.
+//
+// Unpacking: a voltage byte (bits 7..4 real, 3..0 imaginary, two's complement) is decoded
+// exactly into FP16 by placing the real nibble in the mantissa of 1024 (ulp 1, nibble four
+// bits up: 1024 + 16 (re ^ 8)) and the imaginary nibble in the mantissa of 16384 (ulp 16:
+// 16384 + 16 (im ^ 8)), then subtracting 1152 and 16512: (16 re, 16 im), both exact. The
+// factor 16 is folded into the FP16 weights (w / 16, a power of two, so the products
+// round as w x would).
+//
+// Roles (9 warps, 288 threads, two CTAs per SM by tensor memory: 256 columns each):
+//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-2
+//              (D2[(P-2)%2] -> registers), lane quarter = warp;
+//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]), lane quarter = warp-4;
+//   warp 8     one thread: bulk copies of the raw bytes (2 KB per pair, a ring of R
+//              stages), MMA1(P), MMA2(P-1), commits.
+// Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Every wait is
+// bounded by one second of device time; on timeout the CTA records FFTBF_ETIMEOUT, every
+// role leaves its loop, the issuing thread waits (bounded) for its copies and MMAs in
+// flight, and the tensor memory is freed before exit.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "beam_fp32.cuh"
+#include "tc_ptx.cuh"
+
+namespace fftbf {
+
+namespace tcw {
+constexpr int NT = 288;
+constexpr int R = 4;                          // raw-byte ring stages (2 KB each)
+constexpr int NANT = 1024;                    // feeds of the 4x256 lattice
+constexpr uint32_t TMEM_COLS = 256;           // D1[2] at 0, 64; D2[2] at 128, 192
+// MN-major operand tiles (128 rows x 32 K, 16-bit): element (m, k) at
+//   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
+constexpr int SBO = 128, LBO = 2048, TILE = 8192;
+constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
+enum { RAWF = 0, RAWE = RAWF + R, A1F = RAWE + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + 2,
+       A2F = D1E + 2, A2E = A2F + 2, D2F = A2E + 2, D2E = D2F + 2, NBAR = D2E + 2 };
+constexpr uint64_t WAIT_NS = 1000000000ull;
+
+struct Smem {
+  int a1, a2, b1, b2, w, raw, bars, misc, total;
+};
+__host__ __device__ inline Smem layout() {
+  Smem L;
+  int o = 0;
+  auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
+  L.a1 = take(2 * TILE);                 // A1[b]
+  L.a2 = take(4 * TILE);                 // A2[b][s]
+  L.b1 = take(64 * 32 * 2);
+  L.b2 = take(32 * 32 * 2);
+  L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
+  L.raw = take(R * 2 * NANT);
+  L.bars = take(NBAR * 8);
+  L.misc = take(16);
+  L.total = o;
+  return L;
+}
+}  // namespace tcw
+
+namespace {
+
+__device__ __forceinline__ __half2 as_h2(uint32_t v) { return *reinterpret_cast<__half2*>(&v); }
+__device__ __forceinline__ uint32_t as_u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+// The CTA's sequence of (work item, snapshot pair): items blockIdx.x, + gridDim.x, ...
+struct PairSeq {
+  int64_t item;
+  int q;
+  __device__ void next(int npairs) {
+    if (++q == npairs) {
+      q = 0;
+      item += gridDim.x;
+    }
+  }
+};
+
+// Raw bytes of snapshot g of `item` (snapshot g = time g / npol, pol g % npol).
+__device__ __forceinline__ const uint8_t* snap_ptr(const BeamArgs& a, int64_t item, int g) {
+  return item_volts(a, item, tcw::NANT) + snap_offset(a, g, tcw::NANT);
+}
+
+}  // namespace
+
+template <bool REALW>
+__global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) {
+  using namespace tcw;
+  const BeamArgs& a = ta.b;
+  extern __shared__ __align__(1024) unsigned char smem_tcw[];
+  unsigned char* smem = smem_tcw;
+  const Smem L = layout();
+  unsigned char* a1 = smem + L.a1;
+  unsigned char* a2 = smem + L.a2;
+  unsigned char* raw = smem + L.raw;
+  const __half* wre = reinterpret_cast<const __half*>(smem + L.w);
+  const __half* wim = wre + NANT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint32_t* taddr_sm = reinterpret_cast<uint32_t*>(smem + L.misc);
+  volatile int* abort_sm = reinterpret_cast<volatile int*>(smem + L.misc + 4);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nitems = a.nwin * a.nfreq;
+  const int nsnap = a.n_int * a.npol;
+  const int npairs = (nsnap + 1) / 2;
+  if ((int64_t)blockIdx.x >= nitems) return;
+  const int64_t my_items = (nitems - 1 - blockIdx.x) / gridDim.x + 1;
+  const int64_t total = my_items * npairs;            // snapshot pairs of this CTA
+
+  // ---- set-up: tensor memory, barriers, DFT matrices, weights
+  if (warp == 8) {
+    tc::tmem_alloc(taddr_sm, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < NBAR; ++i) {
+      uint32_t c = 4;                                  // one arrival per warp of a role
+      if ((i >= RAWF && i < RAWF + R) || (i >= A1E && i < A1E + 2) || (i >= D1F && i < D1F + 2) ||
+          (i >= A2E && i < A2E + 2) || (i >= D2F && i < D2F + 2))
+        c = 1;                                         // expect_tx arrival or MMA commit
+      tc::mbar_init(bars + i, c);
+    }
+    tc::mbar_init_fence();
+    *abort_sm = 0;
+  }
+  {
+    // B1 [n 64][k 32] and B2 [n 32][k 32] row-major -> canonical K-major tiles
+    const uint16_t* src1 = ta.b1;
+    const uint16_t* src2 = ta.b2;
+    for (int i = tid; i < 64 * 16; i += NT) {
+      const int m = i >> 4, k = (i & 15) * 2;
+      *reinterpret_cast<uint32_t*>(smem + L.b1 + tc::kmajor_off(m, k, B_LBO, B_SBO)) =
+          (uint32_t)src1[m * 32 + k] | ((uint32_t)src1[m * 32 + k + 1] << 16);
+    }
+    for (int i = tid; i < 32 * 16; i += NT) {
+      const int m = i >> 4, k = (i & 15) * 2;
+      *reinterpret_cast<uint32_t*>(smem + L.b2 + tc::kmajor_off(m, k, B_LBO, B_SBO)) =
+          (uint32_t)src2[m * 32 + k] | ((uint32_t)src2[m * 32 + k + 1] << 16);
+    }
+    // weights x scale / 16 in FP16 (the unpacked voltages carry a factor 16)
+    __half* w16 = reinterpret_cast<__half*>(smem + L.w);
+    const float sc = ta.scale * 0.0625f;
+    for (int i = tid; i < NANT; i += NT) {
+      const float2 w = a.w[i];
+      w16[i] = __float2half_rn(w.x * sc);
+      w16[NANT + i] = __float2half_rn(w.y * sc);
+    }
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *taddr_sm;
+  auto fail = [&]() {
+    *abort_sm = 1;
+    atomicExch(ta.err, FFTBF_ETIMEOUT);
+  };
+  auto wait = [&](int bar, uint32_t parity) -> bool {
+    if (tc::mbar_wait_abortable(bars + bar, parity, WAIT_NS, abort_sm)) return true;
+    fail();
+    return false;
+  };
+  // the same, agreed by the whole warp (a lane never leaves a role loop alone, so that the
+  // warp's __syncwarp calls always see every lane)
+  auto wait_warp = [&](int bar, uint32_t parity) -> bool {
+    return __all_sync(0xffffffffu, wait(bar, parity)) != 0;
+  };
+
+  if (warp < 4) {
+    // ============================================ input stage (pair P) + detection (P-2)
+    const int s = tid >> 6, n1 = (tid & 63) >> 2, qn = tid & 3;
+    // A1 offset of this thread's rows (s, A, n2 = 4 qn .. 4 qn + 3) at K element n1
+    const uint32_t a1_off = (uint32_t)((qn & 1) * 8 + (n1 & 7) * 16 + (s * 8 + (qn >> 1)) * SBO +
+                                       (n1 >> 3) * LBO);
+    const int feed0 = 16 * n1 + 4 * qn;
+    // weights of this thread's 16 feeds, as half2 pairs of adjacent N-S feeds
+    uint32_t wr[4][2], wi[4][2];
+#pragma unroll
+    for (int ix = 0; ix < 4; ++ix) {
+      const uint2 v = *reinterpret_cast<const uint2*>(wre + ix * 256 + feed0);
+      wr[ix][0] = v.x;
+      wr[ix][1] = v.y;
+      if constexpr (!REALW) {
+        const uint2 u = *reinterpret_cast<const uint2*>(wim + ix * 256 + feed0);
+        wi[ix][0] = u.x;
+        wi[ix][1] = u.y;
+      }
+    }
+    float2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
+    PairSeq in{(int64_t)blockIdx.x, 0}, de{(int64_t)blockIdx.x, 0};
+    bool ok = true;
+    for (int64_t P = 0; P < total + 2 && ok; ++P) {
+      if (P < total) {
+        // ---------------- input stage of pair P
+        const int b = (int)(P & 1), r = (int)(P % R);
+        const uint32_t u = (uint32_t)(P >> 1);
+        if (!wait_warp(RAWF + r, (uint32_t)((P / R) & 1))) { ok = false; break; }
+        if (u >= 1 && !wait_warp(A1E + b, (u - 1) & 1)) { ok = false; break; }
+        const bool valid = s == 0 || 2 * in.q + 1 < nsnap;
+        uint32_t o[4][2][2];                               // [A][re, im][n2 pair]
+        if (valid) {
+          uint32_t word[4];
+#pragma unroll
+          for (int ix = 0; ix < 4; ++ix)
+            word[ix] = *reinterpret_cast<const uint32_t*>(raw + r * 2 * NANT + s * NANT + ix * 256 + feed0);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            __half2 zr[4], zi[4];
+#pragma unroll
+            for (int ix = 0; ix < 4; ++ix) {
+              // bytes of feeds n2 = 4 qn + 2h, + 1 beside 0x64 bytes: [0x64 b1 0x64 b0]
+              const uint32_t t = __byte_perm(word[ix], 0x64646464u, h ? 0x4342u : 0x4140u);
+              const __half2 re = __hsub2(as_h2((t & 0xFFF0FFF0u) ^ 0x00800080u), as_h2(0x64806480u));
+              const __half2 im = __hsub2(as_h2((t & 0x000F000Fu) ^ 0x74087408u), as_h2(0x74087408u));
+              if constexpr (REALW) {
+                zr[ix] = __hmul2_rn(re, as_h2(wr[ix][h]));
+                zi[ix] = __hmul2_rn(im, as_h2(wr[ix][h]));
+              } else {
+                const __half2 w_r = as_h2(wr[ix][h]), w_i = as_h2(wi[ix][h]);
+                zr[ix] = __hfma2(__hneg2(im), w_i, __hmul2_rn(re, w_r));
+                zi[ix] = __hfma2(im, w_r, __hmul2_rn(re, w_i));
+              }
+            }
+            // 4-point E-W DFT, Y_A = sum_ix z_ix (-i)^(A ix), planar
+            const __half2 ar = __hadd2(zr[0], zr[2]), ai = __hadd2(zi[0], zi[2]);
+            const __half2 br = __hsub2(zr[0], zr[2]), bi = __hsub2(zi[0], zi[2]);
+            const __half2 cr = __hadd2(zr[1], zr[3]), ci = __hadd2(zi[1], zi[3]);
+            const __half2 dr = __hsub2(zr[1], zr[3]), di = __hsub2(zi[1], zi[3]);
+            o[0][0][h] = as_u(__hadd2(ar, cr));
+            o[0][1][h] = as_u(__hadd2(ai, ci));
+            o[2][0][h] = as_u(__hsub2(ar, cr));
+            o[2][1][h] = as_u(__hsub2(ai, ci));
+            o[1][0][h] = as_u(__hadd2(br, di));            // b - i d
+            o[1][1][h] = as_u(__hsub2(bi, dr));
+            o[3][0][h] = as_u(__hsub2(br, di));            // b + i d
+            o[3][1][h] = as_u(__hadd2(bi, dr));
+          }
+        } else {
+#pragma unroll
+          for (int A = 0; A < 4; ++A)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) o[A][c][0] = o[A][c][1] = 0u;
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bars + RAWE + r);   // raw stage r may be refilled
+        unsigned char* dst = a1 + b * TILE + a1_off;
+#pragma unroll
+        for (int A = 0; A < 4; ++A)
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+            *reinterpret_cast<uint2*>(dst + A * 2 * SBO + c * 2 * LBO) = make_uint2(o[A][c][0], o[A][c][1]);
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bars + A1F + b);
+        in.next(npairs);
+      }
+      if (P >= 2) {
+        // ---------------- detection of pair P - 2: |X|^2 of both snapshots
+        const int64_t Pd = P - 2;
+        const int b = (int)(Pd & 1);
+        const uint32_t u = (uint32_t)(Pd >> 1);
+        if (!wait_warp(D2F + b, u & 1)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 128 + 64 * b;
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          uint32_t v[32];
+          tc::tmem_ld32(taddr + 32 * ss, v);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 x = make_float2(__uint_as_float(v[2 * k2]), __uint_as_float(v[2 * k2 + 1]));
+            acc[k2] = __ffma2_rn(x, x, acc[k2]);
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bars + D2E + b);
+        if (de.q == npairs - 1) {
+          // last pair of the window: beams[item][A = warp][k1 = lane + 32 k2]
+          float* dst = a.beams + de.item * (int64_t)(4 * 512) + warp * 512 + lane;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            dst[32 * k2] = (acc[k2].x + acc[k2].y) * inv_s2;
+            acc[k2] = make_float2(0.f, 0.f);
+          }
+        }
+        de.next(npairs);
+      }
+    }
+  } else if (warp < 8) {
+    // ============================================ stage-1 drain: twiddle, A2 (pair P)
+    const int m = tid - 128;                          // TMEM row (s, A, n2)
+    const int s = m >> 6, A = (m >> 4) & 3, n2 = m & 15;
+    const int lq = warp - 4;
+    // twiddles W512^(n2 k1) of this row, half2 pairs over adjacent k1
+    uint32_t ch[16], dh[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      ch[j] = ta.tw16[(n2 * 16 + j) * 2];
+      dh[j] = ta.tw16[(n2 * 16 + j) * 2 + 1];
+    }
+    // A2 offset of element (m2 = A 32 + k1, k = n2) for k1 = 0 and the real part
+    const uint32_t a2_off = (uint32_t)((n2 & 7) * 16 + (4 * A) * SBO + (n2 >> 3) * LBO + s * TILE);
+    for (int64_t P = 0; P < total; ++P) {
+      const int b = (int)(P & 1);
+      const uint32_t u = (uint32_t)(P >> 1);
+      if (!wait_warp(D1F + b, u & 1)) break;
+      if (u >= 1 && !wait_warp(A2E + b, (u - 1) & 1)) break;
+      tc::fence_after_sync();
+      const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 64 * b;
+      unsigned char* dst = a2 + 2 * b * TILE + a2_off;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {                        // k1 = 16 hh .. 16 hh + 15
+        uint32_t xr[16], xi[16];
+        tc::tmem_ld16(taddr + 16 * hh, xr);
+        tc::tmem_ld16(taddr + 32 + 16 * hh, xi);
+        tc::tmem_wait_ld();
+        if (hh == 1) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(bars + D1E + b);     // D1[b] may be overwritten
+        }
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq) {                      // k1 = 8q .. 8q + 7
+          const int q = 2 * hh + qq;
+          uint32_t tr[4], ti[4];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * q + jj, jl = 4 * qq + jj;
+            const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
+            const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
+            const __half2 c = as_h2(ch[j]), d = as_h2(dh[j]);
+            tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
+            ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
+          }
+          *reinterpret_cast<uint4*>(dst + q * SBO) = make_uint4(tr[0], tr[1], tr[2], tr[3]);
+          *reinterpret_cast<uint4*>(dst + q * SBO + 2 * LBO) = make_uint4(ti[0], ti[1], ti[2], ti[3]);
+        }
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(bars + A2F + b);
+    }
+  } else if (lane == 0) {
+    // ============================================ copies and MMAs (one thread)
+    const uint32_t id1 = tc::idesc_f16(128, 64, false) | (1u << 15);   // A MN-major
+    const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);
+    const uint32_t sa1 = tc::smem_u32(a1), sa2 = tc::smem_u32(a2);
+    const uint32_t sb1 = tc::smem_u32(smem + L.b1), sb2 = tc::smem_u32(smem + L.b2);
+    PairSeq cp{(int64_t)blockIdx.x, 0};
+    int64_t issued = 0;                                // pairs whose bytes were requested
+    auto copy = [&](int64_t P) {
+      const int r = (int)(P % R);
+      unsigned char* dst = raw + r * 2 * NANT;
+      const int g = 2 * cp.q;
+      const uint8_t* s0 = snap_ptr(a, cp.item, g);
+      if (g + 1 < nsnap) {
+        const uint8_t* s1 = snap_ptr(a, cp.item, g + 1);
+        tc::mbar_arrive_expect_tx(bars + RAWF + r, 2 * NANT);
+        if (s1 == s0 + NANT) {
+          tc::bulk_g2s(dst, s0, 2 * NANT, bars + RAWF + r);
+        } else {
+          tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
+          tc::bulk_g2s(dst + NANT, s1, NANT, bars + RAWF + r);
+        }
+      } else {
+        tc::mbar_arrive_expect_tx(bars + RAWF + r, NANT);
+        tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
+      }
+      cp.next(npairs);
+      ++issued;
+    };
+    bool ok = true;
+    for (int64_t P = 0; P < total && P < R; ++P) copy(P);
+    int64_t mma1 = 0, mma2 = 0;                        // MMAs issued
+    for (int64_t P = 0; P <= total && ok; ++P) {
+      if (P < total) {
+        const int b = (int)(P & 1);
+        const uint32_t u = (uint32_t)(P >> 1);
+        if (!wait(A1F + b, u & 1) || (u >= 1 && !wait(D1E + b, (u - 1) & 1))) { ok = false; break; }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+          tc::mma_f16(tbase + 64 * b, tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO),
+                      tc::smem_desc(sb1 + kk * 2 * B_LBO, B_LBO, B_SBO), id1, kk);
+        tc::mma_commit(bars + D1F + b);
+        tc::mma_commit(bars + A1E + b);
+        ++mma1;
+        // refill the raw stage pair P has consumed (its input stage arrived before A1F)
+        if (issued < total) {
+          const int r = (int)(issued % R);
+          if (!wait(RAWE + r, (uint32_t)(((issued / R) - 1) & 1))) { ok = false; break; }
+          copy(issued);
+        }
+      }
+      if (P >= 1) {
+        const int64_t Q = P - 1;
+        const int b = (int)(Q & 1);
+        const uint32_t u = (uint32_t)(Q >> 1);
+        if (!wait(A2F + b, u & 1) || (u >= 1 && !wait(D2E + b, (u - 1) & 1))) { ok = false; break; }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss)
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc::mma_f16(tbase + 128 + 64 * b + 32 * ss,
+                        tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO),
+                        tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO), id2, kk);
+        tc::mma_commit(bars + D2F + b);
+        tc::mma_commit(bars + A2E + b);
+        ++mma2;
+      }
+    }
+    // Every copy and MMA issued must have landed before the CTA frees its memory. On the
+    // normal path the other roles already waited for all of them; after a timeout, wait
+    // here (bounded, regardless of the abort flag) for the last ones of each ring.
+    for (int64_t k = issued - 1; k >= 0 && k >= issued - R; --k)
+      tc::mbar_wait(bars + RAWF + (int)(k % R), (uint32_t)((k / R) & 1), WAIT_NS);
+    if (mma1 > 0) tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & 1), (uint32_t)(((mma1 - 1) >> 1) & 1), WAIT_NS);
+    if (mma2 > 0) tc::mbar_wait(bars + D2F + (int)((mma2 - 1) & 1), (uint32_t)(((mma2 - 1) >> 1) & 1), WAIT_NS);
+  }
+  __syncwarp();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 8) tc::tmem_dealloc(tbase, TMEM_COLS);
+}
+
+bool tcw_eligible(const TcArgs& ta) {
+  const BeamArgs& a = ta.b;
+  return !ta.bf16 && !ta.split && ta.tw16 && a.nx == 4 && a.ny == 256 && a.mx == 4 &&
+         a.my == 512 && a.nyf == 256 && a.ew_dft &&
+         (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
+}
+
+int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st) {
+  const BeamArgs& a = ta.b;
+  const int64_t items = a.nwin * a.nfreq;
+  if (items <= 0) return FFTBF_OK;
+  const tcw::Smem L = tcw::layout();
+  // two CTAs per SM (256 of the 512 tensor-memory columns each): keep a third from
+  // fitting by shared memory as well
+  size_t smem = (size_t)L.total;
+  if (smem < 77 * 1024) smem = 77 * 1024;
+  auto kern = a.real_w ? beams_tcw_kernel<true> : beams_tcw_kernel<false>;
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared));
+  const int64_t grid = items < (int64_t)nsm * 2 ? items : (int64_t)nsm * 2;
+  kern<<<(unsigned)grid, tcw::NT, smem, st>>>(ta);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+// ---------------------------------------------------------------- plan tables --
+// Stage matrices of the warp-specialised FP16 form, row-major [n][k] (n = output, k =
+// input), FP64 rounded once to FP16, and the W512 twiddle pairs:
+//   b1[n = co 32 + k1][k = ci 16 + n1]   W32^(n1 k1), planar in and out
+//   b2[n = 2 k2 + co][k = ci 16 + n2]    W16^(n2 k2), planar in, interleaved out
+//   tw16[(n2 16 + j) 2 + {0, 1}]         (cos, cos) and (-sin, -sin) of 2 pi n2 k1 / 512 for
+//                                        k1 = 2j, 2j + 1, as half2
+// With W = C + iS (S = -sin): out_re = sum in_re C - in_im S, out_im = sum in_re S + in_im C.
+__global__ void tcw_tables_kernel(uint16_t* b1, uint16_t* b2, uint32_t* tw16) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  auto h = [](double v) {
+    __half x = __float2half_rn((float)v);
+    return *reinterpret_cast<uint16_t*>(&x);
+  };
+  auto entry = [](int co, int ci, double c, double sp) {
+    if (co == 0) return ci == 0 ? c : -sp;
+    return ci == 0 ? sp : c;
+  };
+  if (i < 64 * 32) {
+    const int n = i >> 5, k = i & 31;
+    const int co = n >> 5, k1 = n & 31, ci = k >> 4, n1 = k & 15;
+    double sn, cs;
+    sincospi(2.0 * ((n1 * k1) % 32) / 32.0, &sn, &cs);
+    b1[i] = h(entry(co, ci, cs, -sn));
+  }
+  if (i < 32 * 32) {
+    const int n = i >> 5, k = i & 31;
+    const int k2 = n >> 1, co = n & 1, ci = k >> 4, n2 = k & 15;
+    double sn, cs;
+    sincospi(2.0 * ((n2 * k2) % 16) / 16.0, &sn, &cs);
+    b2[i] = h(entry(co, ci, cs, -sn));
+  }
+  if (i < 16 * 16) {
+    const int n2 = i >> 4, j = i & 15;
+    double s0, c0, s1, c1;
+    sincospi(2.0 * ((n2 * 2 * j) % 512) / 512.0, &s0, &c0);
+    sincospi(2.0 * ((n2 * (2 * j + 1)) % 512) / 512.0, &s1, &c1);
+    tw16[2 * i] = (uint32_t)h(c0) | ((uint32_t)h(c1) << 16);
+    tw16[2 * i + 1] = (uint32_t)h(-s0) | ((uint32_t)h(-s1) << 16);
+  }
+}
+
+int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, cudaStream_t st) {
+  tcw_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, tw16);
+  FFTBF_CUDA_TRY(cudaGetLastError());
+  return FFTBF_OK;
+}
+
+}  // namespace fftbf

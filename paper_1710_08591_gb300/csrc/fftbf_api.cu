@@ -151,6 +151,15 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
     rc = build_tc_tables_lo(p->d_b1lo, p->d_b2lo, 0);
     if (rc != FFTBF_OK) return rc;
   }
+  if (prec == FFTBF_PREC_TC_FP16) {
+    if (!p->d_b1w) {
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_b1w, sizeof(uint16_t) * 64 * 32));
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_b2w, sizeof(uint16_t) * 32 * 32));
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_tw16, sizeof(uint32_t) * 16 * 16 * 2));
+    }
+    rc = build_tcw_tables(p->d_b1w, p->d_b2w, p->d_tw16, 0);
+    if (rc != FFTBF_OK) return rc;
+  }
   FFTBF_CUDA_TRY(cudaDeviceSynchronize());
   // FP16 range: |X1| <= 16 * max_iy sum_ix |w| * 8 sqrt(2); keep it below 30000.
   double wmax = 0.0;
@@ -213,6 +222,11 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
             (p->ny & 3) == 0 && a.nyf == p->ny;
     ta.b1lo = p->d_b1lo;
     ta.b2lo = p->d_b2lo;
+    if (p->precision == FFTBF_PREC_TC_FP16) {
+      ta.b1w = p->d_b1w;
+      ta.b2w = p->d_b2w;
+      ta.tw16 = p->d_tw16;
+    }
     rc = launch_beams_tc(ta, p->nsm, st);
   }
   if (rc == FFTBF_OK) remember_stream(p, st);
@@ -303,6 +317,9 @@ void fftbf_destroy(fftbf_plan* p) {
     cudaFree(p->d_b2);
     cudaFree(p->d_b1lo);
     cudaFree(p->d_b2lo);
+    cudaFree(p->d_b1w);
+    cudaFree(p->d_b2w);
+    cudaFree(p->d_tw16);
     cudaFree(p->d_err);
   }
   delete p;
@@ -340,7 +357,11 @@ int fftbf_debug_tc_gemm(const uint16_t* a, const uint16_t* b, int n, int bf16, i
   int* err = nullptr;
   FFTBF_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
   cudaMemsetAsync(err, 0, sizeof(int), st);
-  int rc = launch_debug_tc_gemm(a, b, n, bf16 != 0, padded != 0, d, err, st);
+  if (padded < 0 || padded > 2) {
+    cudaFree(err);
+    return set_error(FFTBF_EINVAL, "layout must be 0, 1 or 2");
+  }
+  int rc = launch_debug_tc_gemm(a, b, n, bf16 != 0, padded, d, err, st);
   int h = 0;
   if (rc == FFTBF_OK) {
     cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);

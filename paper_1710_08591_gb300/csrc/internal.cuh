@@ -91,12 +91,19 @@ struct TcArgs {
   int w4;               // FP16 form with real weights on the packed-half input stage
   const uint16_t* b1lo;
   const uint16_t* b2lo;
+  // warp-specialised FP16 kernel (4x256 lattice): planar stage matrices and W512 twiddles
+  const uint16_t* b1w;  // [64][32]
+  const uint16_t* b2w;  // [32][32]
+  const uint32_t* tw16; // [16 n2][16 k1 pairs][2] half2 (cos, -sin)
 };
 bool tc_supported(int nx, int ny, int mx, int my);
 int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st);
 int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st);
 int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st);
-int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, bool padded,
+bool tcw_eligible(const TcArgs& ta);
+int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st);
+int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, cudaStream_t st);
+int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, int layout,
                          float* D, int* err, cudaStream_t st);
 int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st);
 // FP64 table builders (device), rounded to FP32.
@@ -194,6 +201,9 @@ struct fftbf_plan {
   uint16_t* d_b2 = nullptr;
   uint16_t* d_b1lo = nullptr;     // split FP16 form: residuals of the stage matrices
   uint16_t* d_b2lo = nullptr;
+  uint16_t* d_b1w = nullptr;      // warp-specialised FP16 kernel: planar stage matrices
+  uint16_t* d_b2w = nullptr;
+  uint32_t* d_tw16 = nullptr;     // and its W512 twiddle pairs
   float tc_scale = 1.f;
   int* d_err = nullptr;           // device error word of bounded waits
   std::vector<cudaStream_t> streams_used;

@@ -57,16 +57,23 @@ def test_server_faults_leave_other_frames_unchanged():
             fb.server_submit(sv, 3, good[0], np.empty((nf, nx, 128), np.float32))
         with pytest.raises(ValueError):
             fb.server_submit(sv, 0, good[0][:, ::2], np.empty((nf, nx, 128), np.float32))
-        # a wait that cannot be met in time reports ETIMEOUT; the frames still complete
+        # a wait that cannot be met in time reports ETIMEOUT (the server is held, so the
+        # frames are staged but not launched); released, the frames still complete
         outs = []
         tickets = []
+        fb.server_hold(sv, True)
         for fr in good:
             o = np.empty((nf, nx, 128), np.float32)
             tickets.append(fb.server_submit(sv, 0, fr, o))
             outs.append(o)
         with pytest.raises(fb.FftbfError) as e:
-            fb.server_wait(sv, tickets[-1] + 1000, 0.05)   # a ticket that never completes
+            fb.server_wait(sv, tickets[-1], 0.05)
         assert e.value.code == -4
+        # a ticket that was never issued is refused, not waited for
+        with pytest.raises(fb.FftbfError) as e:
+            fb.server_wait(sv, tickets[-1] + 1000, 0.05)
+        assert e.value.code == -1
+        fb.server_hold(sv, False)
         fb.server_wait(sv, -1, 60.0)
         for o, r in zip(outs, ref):
             assert np.array_equal(o, r)

@@ -31,7 +31,7 @@ def _lib():
 
 
 @pytest.mark.parametrize("bf16", [False, True], ids=["fp16", "bf16"])
-@pytest.mark.parametrize("padded", [False, True], ids=["canon", "padded"])
+@pytest.mark.parametrize("padded", [0, 1, 2], ids=["canon", "padded", "mn-major"])
 @pytest.mark.parametrize("n", [32, 64, 128])
 def test_tc_gemm_building_block(bf16, padded, n):
     rng = np.random.default_rng(n + 2 * padded + bf16)
