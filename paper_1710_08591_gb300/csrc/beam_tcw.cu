@@ -28,9 +28,9 @@
 // round as w x would).
 //
 // Roles (9 warps, 288 threads, two CTAs per SM by tensor memory: 256 columns each):
-//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-2
-//              (D2[(P-2)%2] -> registers), lane quarter = warp;
-//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]), lane quarter = warp-4;
+//   warps 0-3  input stage of pair P (bytes -> A1[P%2]);
+//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]) and detection of
+//              pair P-2 (D2[(P-2)%2] -> registers), lane quarter = warp-4;
 //   warp 8     one thread: bulk copies of the raw bytes (2 KB per pair, a ring of R
 //              stages), MMA1(P), MMA2(P-1), commits.
 // Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Every wait is
@@ -47,7 +47,7 @@ namespace fftbf {
 
 namespace tcw {
 constexpr int NT = 288;
-constexpr int R = 4;                          // raw-byte ring stages (2 KB each)
+constexpr int R = 8;                          // raw-byte ring stages (2 KB each)
 constexpr int NANT = 1024;                    // feeds of the 4x256 lattice
 constexpr uint32_t TMEM_COLS = 256;           // D1[2] at 0, 64; D2[2] at 128, 192
 // MN-major operand tiles (128 rows x 32 K, 16-bit): element (m, k) at
@@ -59,7 +59,7 @@ enum { RAWF = 0, RAWE = RAWF + R, A1F = RAWE + R, A1E = A1F + 2, D1F = A1E + 2, 
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 struct Smem {
-  int a1, a2, b1, b2, w, raw, bars, misc, total;
+  int a1, a2, b1, b2, w, tw, raw, bars, misc, total;
 };
 __host__ __device__ inline Smem layout() {
   Smem L;
@@ -70,6 +70,7 @@ __host__ __device__ inline Smem layout() {
   L.b1 = take(64 * 32 * 2);
   L.b2 = take(32 * 32 * 2);
   L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
+  L.tw = take(16 * 4 * 8 * 4);           // W512 twiddles [n2][k1 chunk q][cos x4, -sin x4]
   L.raw = take(R * 2 * NANT);
   L.bars = take(NBAR * 8);
   L.misc = take(16);
@@ -94,11 +95,6 @@ struct PairSeq {
     }
   }
 };
-
-// Raw bytes of snapshot g of `item` (snapshot g = time g / npol, pol g % npol).
-__device__ __forceinline__ const uint8_t* snap_ptr(const BeamArgs& a, int64_t item, int g) {
-  return item_volts(a, item, tcw::NANT) + snap_offset(a, g, tcw::NANT);
-}
 
 }  // namespace
 
@@ -163,6 +159,13 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       w16[i] = __float2half_rn(w.x * sc);
       w16[NANT + i] = __float2half_rn(w.y * sc);
     }
+    // twiddle pairs of row n2 for the k1 chunk q (pairs j = 4q .. 4q+3): cos x4, -sin x4
+    uint32_t* tws = reinterpret_cast<uint32_t*>(smem + L.tw);
+    for (int i = tid; i < 16 * 16; i += NT) {
+      const int n2 = i >> 4, j = i & 15, q = j >> 2, jj = j & 3;
+      tws[(n2 * 4 + q) * 8 + jj] = ta.tw16[i * 2];
+      tws[(n2 * 4 + q) * 8 + 4 + jj] = ta.tw16[i * 2 + 1];
+    }
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -204,14 +207,10 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         wi[ix][1] = u.y;
       }
     }
-    float2 acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
-    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
-    PairSeq in{(int64_t)blockIdx.x, 0}, de{(int64_t)blockIdx.x, 0};
+    PairSeq in{(int64_t)blockIdx.x, 0};
     bool ok = true;
-    for (int64_t P = 0; P < total + 2 && ok; ++P) {
-      if (P < total) {
+    for (int64_t P = 0; P < total && ok; ++P) {
+      {
         // ---------------- input stage of pair P
         const int b = (int)(P & 1), r = (int)(P % R);
         const uint32_t u = (uint32_t)(P >> 1);
@@ -275,6 +274,65 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         if (lane == 0) tc::mbar_arrive(bars + A1F + b);
         in.next(npairs);
       }
+    }
+  } else if (warp < 8) {
+    // ============================================ stage-1 drain: twiddle, A2 (pair P)
+    const int m = tid - 128;                          // TMEM row (s, A, n2)
+    const int s = m >> 6, A = (m >> 4) & 3, n2 = m & 15;
+    const int lq = warp - 4;
+    // twiddles W512^(n2 k1) of this row: half2 pairs over adjacent k1, by chunks of 8 k1
+    const uint4* tw4 = reinterpret_cast<const uint4*>(smem + L.tw) + n2 * 8;
+    // A2 offset of element (m2 = A 32 + k1, k = n2) for k1 = 0 and the real part
+    const uint32_t a2_off = (uint32_t)((n2 & 7) * 16 + (4 * A) * SBO + (n2 >> 3) * LBO + s * TILE);
+    float2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
+    PairSeq de{(int64_t)blockIdx.x, 0};
+    bool ok = true;
+    for (int64_t P = 0; P < total + 2 && ok; ++P) {
+      if (P < total) {
+        const int b = (int)(P & 1);
+        const uint32_t u = (uint32_t)(P >> 1);
+        if (!wait_warp(D1F + b, u & 1)) { ok = false; break; }
+        if (u >= 1 && !wait_warp(A2E + b, (u - 1) & 1)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 64 * b;
+        unsigned char* dst = a2 + 2 * b * TILE + a2_off;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {                        // k1 = 16 hh .. 16 hh + 15
+          uint32_t xr[16], xi[16];
+          tc::tmem_ld16(taddr + 16 * hh, xr);
+          tc::tmem_ld16(taddr + 32 + 16 * hh, xi);
+          tc::tmem_wait_ld();
+          if (hh == 1) {
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(bars + D1E + b);     // D1[b] may be overwritten
+          }
+#pragma unroll
+          for (int qq = 0; qq < 2; ++qq) {                      // k1 = 8q .. 8q + 7
+            const int q = 2 * hh + qq;
+            const uint4 cq = tw4[2 * q], dq = tw4[2 * q + 1];
+            const uint32_t cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {dq.x, dq.y, dq.z, dq.w};
+            uint32_t tr[4], ti[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int jl = 4 * qq + jj;
+              const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
+              const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
+              const __half2 c = as_h2(cv[jj]), d = as_h2(dv[jj]);
+              tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
+              ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
+            }
+            *reinterpret_cast<uint4*>(dst + q * SBO) = make_uint4(tr[0], tr[1], tr[2], tr[3]);
+            *reinterpret_cast<uint4*>(dst + q * SBO + 2 * LBO) = make_uint4(ti[0], ti[1], ti[2], ti[3]);
+          }
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bars + A2F + b);
+      }
       if (P >= 2) {
         // ---------------- detection of pair P - 2: |X|^2 of both snapshots
         const int64_t Pd = P - 2;
@@ -282,7 +340,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         const uint32_t u = (uint32_t)(Pd >> 1);
         if (!wait_warp(D2F + b, u & 1)) { ok = false; break; }
         tc::fence_after_sync();
-        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 128 + 64 * b;
+        const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 128 + 64 * b;
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss) {
           uint32_t v[32];
@@ -298,8 +356,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(bars + D2E + b);
         if (de.q == npairs - 1) {
-          // last pair of the window: beams[item][A = warp][k1 = lane + 32 k2]
-          float* dst = a.beams + de.item * (int64_t)(4 * 512) + warp * 512 + lane;
+          // last pair of the window: beams[item][A = lq][k1 = lane + 32 k2]
+          float* dst = a.beams + de.item * (int64_t)(4 * 512) + lq * 512 + lane;
 #pragma unroll
           for (int k2 = 0; k2 < 16; ++k2) {
             dst[32 * k2] = (acc[k2].x + acc[k2].y) * inv_s2;
@@ -309,128 +367,123 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         de.next(npairs);
       }
     }
-  } else if (warp < 8) {
-    // ============================================ stage-1 drain: twiddle, A2 (pair P)
-    const int m = tid - 128;                          // TMEM row (s, A, n2)
-    const int s = m >> 6, A = (m >> 4) & 3, n2 = m & 15;
-    const int lq = warp - 4;
-    // twiddles W512^(n2 k1) of this row, half2 pairs over adjacent k1
-    uint32_t ch[16], dh[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      ch[j] = ta.tw16[(n2 * 16 + j) * 2];
-      dh[j] = ta.tw16[(n2 * 16 + j) * 2 + 1];
-    }
-    // A2 offset of element (m2 = A 32 + k1, k = n2) for k1 = 0 and the real part
-    const uint32_t a2_off = (uint32_t)((n2 & 7) * 16 + (4 * A) * SBO + (n2 >> 3) * LBO + s * TILE);
-    for (int64_t P = 0; P < total; ++P) {
-      const int b = (int)(P & 1);
-      const uint32_t u = (uint32_t)(P >> 1);
-      if (!wait_warp(D1F + b, u & 1)) break;
-      if (u >= 1 && !wait_warp(A2E + b, (u - 1) & 1)) break;
-      tc::fence_after_sync();
-      const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 64 * b;
-      unsigned char* dst = a2 + 2 * b * TILE + a2_off;
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {                        // k1 = 16 hh .. 16 hh + 15
-        uint32_t xr[16], xi[16];
-        tc::tmem_ld16(taddr + 16 * hh, xr);
-        tc::tmem_ld16(taddr + 32 + 16 * hh, xi);
-        tc::tmem_wait_ld();
-        if (hh == 1) {
-          tc::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(bars + D1E + b);     // D1[b] may be overwritten
-        }
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq) {                      // k1 = 8q .. 8q + 7
-          const int q = 2 * hh + qq;
-          uint32_t tr[4], ti[4];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int j = 4 * q + jj, jl = 4 * qq + jj;
-            const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
-            const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
-            const __half2 c = as_h2(ch[j]), d = as_h2(dh[j]);
-            tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
-            ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
-          }
-          *reinterpret_cast<uint4*>(dst + q * SBO) = make_uint4(tr[0], tr[1], tr[2], tr[3]);
-          *reinterpret_cast<uint4*>(dst + q * SBO + 2 * LBO) = make_uint4(ti[0], ti[1], ti[2], ti[3]);
-        }
-      }
-      tc::fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(bars + A2F + b);
-    }
   } else if (lane == 0) {
     // ============================================ copies and MMAs (one thread)
     const uint32_t id1 = tc::idesc_f16(128, 64, false) | (1u << 15);   // A MN-major
     const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);
     const uint32_t sa1 = tc::smem_u32(a1), sa2 = tc::smem_u32(a2);
     const uint32_t sb1 = tc::smem_u32(smem + L.b1), sb2 = tc::smem_u32(smem + L.b2);
+    // raw-byte source of the next pair to copy: the item's first byte is found once per
+    // item (one 64-bit division), pairs then advance by a constant stride
     PairSeq cp{(int64_t)blockIdx.x, 0};
+    const uint8_t* ibase = item_volts(a, cp.item, NANT);
+    const int64_t tstride = (int64_t)a.nfreq * a.npol * NANT;      // one time sample
+    const bool two_pol = a.npol == 2;
     int64_t issued = 0;                                // pairs whose bytes were requested
     auto copy = [&](int64_t P) {
       const int r = (int)(P % R);
       unsigned char* dst = raw + r * 2 * NANT;
       const int g = 2 * cp.q;
-      const uint8_t* s0 = snap_ptr(a, cp.item, g);
+      const uint8_t* s0 = two_pol ? ibase + (int64_t)cp.q * tstride : ibase + snap_offset(a, g, NANT);
       if (g + 1 < nsnap) {
-        const uint8_t* s1 = snap_ptr(a, cp.item, g + 1);
         tc::mbar_arrive_expect_tx(bars + RAWF + r, 2 * NANT);
-        if (s1 == s0 + NANT) {
+        if (two_pol) {
           tc::bulk_g2s(dst, s0, 2 * NANT, bars + RAWF + r);
         } else {
           tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
-          tc::bulk_g2s(dst + NANT, s1, NANT, bars + RAWF + r);
+          tc::bulk_g2s(dst + NANT, ibase + snap_offset(a, g + 1, NANT), NANT, bars + RAWF + r);
         }
       } else {
         tc::mbar_arrive_expect_tx(bars + RAWF + r, NANT);
         tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
       }
-      cp.next(npairs);
+      if (++cp.q == npairs) {
+        cp.q = 0;
+        cp.item += gridDim.x;
+        if (cp.item < nitems) ibase = item_volts(a, cp.item, NANT);
+      }
       ++issued;
     };
-    bool ok = true;
-    for (int64_t P = 0; P < total && P < R; ++P) copy(P);
-    int64_t mma1 = 0, mma2 = 0;                        // MMAs issued
-    for (int64_t P = 0; P <= total && ok; ++P) {
-      if (P < total) {
-        const int b = (int)(P & 1);
-        const uint32_t u = (uint32_t)(P >> 1);
-        if (!wait(A1F + b, u & 1) || (u >= 1 && !wait(D1E + b, (u - 1) & 1))) { ok = false; break; }
-        tc::fence_after_sync();
+    // MMA descriptors of every buffer (constant for the launch)
+    uint64_t da1[2][2], da2[2][2][2], db1[2], db2[2];
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
-          tc::mma_f16(tbase + 64 * b, tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO),
-                      tc::smem_desc(sb1 + kk * 2 * B_LBO, B_LBO, B_SBO), id1, kk);
-        tc::mma_commit(bars + D1F + b);
-        tc::mma_commit(bars + A1E + b);
-        ++mma1;
-        // refill the raw stage pair P has consumed (its input stage arrived before A1F)
-        if (issued < total) {
-          const int r = (int)(issued % R);
-          if (!wait(RAWE + r, (uint32_t)(((issued / R) - 1) & 1))) { ok = false; break; }
-          copy(issued);
-        }
-      }
-      if (P >= 1) {
-        const int64_t Q = P - 1;
-        const int b = (int)(Q & 1);
-        const uint32_t u = (uint32_t)(Q >> 1);
-        if (!wait(A2F + b, u & 1) || (u >= 1 && !wait(D2E + b, (u - 1) & 1))) { ok = false; break; }
-        tc::fence_after_sync();
+    for (int kk = 0; kk < 2; ++kk) {
+      db1[kk] = tc::smem_desc(sb1 + kk * 2 * B_LBO, B_LBO, B_SBO);
+      db2[kk] = tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        da1[b][kk] = tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO);
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss)
+          da2[b][ss][kk] = tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO);
+      }
+    }
+    // Event loop: whichever of the next MMA1, the next refill and the next MMA2 has its
+    // inputs ready is issued (non-blocking tests), so that no stream waits behind another.
+    while (issued < total && issued < R) copy(issued);
+    int64_t mma1 = 0, mma2 = 0;                        // MMAs issued
+    uint64_t t_idle = 0;
+    uint32_t idle = 0;
+    while (mma2 < total) {
+      bool prog = false;
+      if (mma1 < total) {
+        const int b = (int)(mma1 & 1);
+        const uint32_t u = (uint32_t)(mma1 >> 1);
+        if (tc::mbar_test(bars + A1F + b, u & 1) && (u == 0 || tc::mbar_test(bars + D1E + b, (u - 1) & 1))) {
+          tc::fence_after_sync();
+          if (b == 0) {
+            tc::mma_f16(tbase, da1[0][0], db1[0], id1, 0);
+            tc::mma_f16(tbase, da1[0][1], db1[1], id1, 1);
+          } else {
+            tc::mma_f16(tbase + 64, da1[1][0], db1[0], id1, 0);
+            tc::mma_f16(tbase + 64, da1[1][1], db1[1], id1, 1);
+          }
+          tc::mma_commit(bars + D1F + b);
+          tc::mma_commit(bars + A1E + b);
+          ++mma1;
+          prog = true;
+        }
+      }
+      // refill the raw stage that pair `issued - R` has been read from
+      if (issued < total && tc::mbar_test(bars + RAWE + (int)(issued % R), (uint32_t)(((issued / R) - 1) & 1))) {
+        copy(issued);
+        prog = true;
+      }
+      if (mma2 < mma1) {
+        const int b = (int)(mma2 & 1);
+        const uint32_t u = (uint32_t)(mma2 >> 1);
+        if (tc::mbar_test(bars + A2F + b, u & 1) && (u == 0 || tc::mbar_test(bars + D2E + b, (u - 1) & 1))) {
+          tc::fence_after_sync();
+          if (b == 0) {
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
-            tc::mma_f16(tbase + 128 + 64 * b + 32 * ss,
-                        tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO),
-                        tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO), id2, kk);
-        tc::mma_commit(bars + D2F + b);
-        tc::mma_commit(bars + A2E + b);
-        ++mma2;
+            for (int ss = 0; ss < 2; ++ss) {
+              tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
+              tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
+            }
+          } else {
+#pragma unroll
+            for (int ss = 0; ss < 2; ++ss) {
+              tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
+              tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
+            }
+          }
+          tc::mma_commit(bars + D2F + b);
+          tc::mma_commit(bars + A2E + b);
+          ++mma2;
+          prog = true;
+        }
+      }
+      if (prog) {
+        idle = 0;
+        continue;
+      }
+      // nothing ready: back off briefly; give up after one second without progress
+      __nanosleep(32);
+      if ((++idle & 63) == 0) {
+        if (*abort_sm) break;
+        const uint64_t t = tc::globaltimer_ns();
+        if (idle == 64) t_idle = t;
+        else if (t - t_idle > WAIT_NS) { fail(); break; }
       }
     }
     // Every copy and MMA issued must have landed before the CTA frees its memory. On the
