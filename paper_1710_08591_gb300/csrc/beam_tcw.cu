@@ -27,16 +27,20 @@
 // factor 16 is folded into the FP16 weights (w / 16, a power of two, so the products
 // round as w x would).
 //
-// Roles (9 warps, 288 threads, two CTAs per SM by tensor memory: 256 columns each):
-//   warps 0-3  input stage of pair P (bytes -> A1[P%2]);
-//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]) and detection of
-//              pair P-2 (D2[(P-2)%2] -> registers), lane quarter = warp-4;
-//   warp 8     one thread: bulk copies of the raw bytes (2 KB per pair, a ring of R
-//              stages), MMA1(P), MMA2(P-1), commits.
-// Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Every wait is
-// bounded by one second of device time; on timeout the CTA records FFTBF_ETIMEOUT, every
-// role leaves its loop, the issuing thread waits (bounded) for its copies and MMAs in
-// flight, and the tensor memory is freed before exit.
+// Roles (10 warps, 320 threads, two CTAs per SM by tensor memory: 256 columns each):
+//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-2
+//              (D2[(P-2)%2] -> registers), lane quarter = warp;
+//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]), lane quarter = warp-4;
+//   warp 8     one thread: MMA1(P) once A1[P%2] is written and D1[P%2] drained, then the
+//              bulk copy of pair P+R's raw bytes into the ring stage pair P was read from
+//              (2 KB per pair, R stages);
+//   warp 9     one thread: MMA2(P) once A2[P%2] is written and D2[P%2] detected.
+// Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Waiting threads
+// are suspended (try_wait with a suspend-time hint) rather than spinning, so waiting warps
+// take no issue slots. Every wait is bounded by one second of device time; on timeout the
+// CTA records FFTBF_ETIMEOUT, every role leaves its loop, the issuing threads wait
+// (bounded) for their copies and MMAs in flight, and the tensor memory is freed before
+// exit.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -46,7 +50,7 @@
 namespace fftbf {
 
 namespace tcw {
-constexpr int NT = 288;
+constexpr int NT = 320;
 constexpr int R = 8;                          // raw-byte ring stages (2 KB each)
 constexpr int NANT = 1024;                    // feeds of the 4x256 lattice
 constexpr uint32_t TMEM_COLS = 256;           // D1[2] at 0, 64; D2[2] at 128, 192
@@ -54,12 +58,12 @@ constexpr uint32_t TMEM_COLS = 256;           // D1[2] at 0, 64; D2[2] at 128, 1
 //   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
 constexpr int SBO = 128, LBO = 2048, TILE = 8192;
 constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
-enum { RAWF = 0, RAWE = RAWF + R, A1F = RAWE + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + 2,
+enum { RAWF = 0, A1F = RAWF + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + 2,
        A2F = D1E + 2, A2E = A2F + 2, D2F = A2E + 2, D2E = D2F + 2, NBAR = D2E + 2 };
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 struct Smem {
-  int a1, a2, b1, b2, w, tw, raw, bars, misc, total;
+  int a1, a2, b1, b2, w, raw, bars, misc, total;
 };
 __host__ __device__ inline Smem layout() {
   Smem L;
@@ -70,7 +74,6 @@ __host__ __device__ inline Smem layout() {
   L.b1 = take(64 * 32 * 2);
   L.b2 = take(32 * 32 * 2);
   L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
-  L.tw = take(16 * 4 * 8 * 4);           // W512 twiddles [n2][k1 chunk q][cos x4, -sin x4]
   L.raw = take(R * 2 * NANT);
   L.bars = take(NBAR * 8);
   L.misc = take(16);
@@ -159,13 +162,6 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       w16[i] = __float2half_rn(w.x * sc);
       w16[NANT + i] = __float2half_rn(w.y * sc);
     }
-    // twiddle pairs of row n2 for the k1 chunk q (pairs j = 4q .. 4q+3): cos x4, -sin x4
-    uint32_t* tws = reinterpret_cast<uint32_t*>(smem + L.tw);
-    for (int i = tid; i < 16 * 16; i += NT) {
-      const int n2 = i >> 4, j = i & 15, q = j >> 2, jj = j & 3;
-      tws[(n2 * 4 + q) * 8 + jj] = ta.tw16[i * 2];
-      tws[(n2 * 4 + q) * 8 + 4 + jj] = ta.tw16[i * 2 + 1];
-    }
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -176,20 +172,24 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     *abort_sm = 1;
     atomicExch(ta.err, FFTBF_ETIMEOUT);
   };
-  auto wait = [&](int bar, uint32_t parity) -> bool {
-    if (tc::mbar_wait_abortable(bars + bar, parity, WAIT_NS, abort_sm)) return true;
+  auto wait_sleep = [&](int bar, uint32_t parity) -> bool {
+    if (tc::mbar_wait_sleep(bars + bar, parity, WAIT_NS, abort_sm)) return true;
     fail();
     return false;
   };
   // the same, agreed by the whole warp (a lane never leaves a role loop alone, so that the
   // warp's __syncwarp calls always see every lane)
   auto wait_warp = [&](int bar, uint32_t parity) -> bool {
-    return __all_sync(0xffffffffu, wait(bar, parity)) != 0;
+    return __all_sync(0xffffffffu, wait_sleep(bar, parity)) != 0;
   };
 
   if (warp < 4) {
     // ============================================ input stage (pair P) + detection (P-2)
-    const int s = tid >> 6, n1 = (tid & 63) >> 2, qn = tid & 3;
+    // thread -> (snapshot s, K element n1, feeds n2 = 4 qn .. 4 qn + 3), chosen so that the
+    // 8-byte A1 stores of each half-warp cover 128 contiguous bytes (no bank conflict)
+    // and a warp's raw-byte loads cover 128 contiguous bytes
+    const int s = tid >> 6, n1 = 8 * ((tid >> 5) & 1) + ((lane >> 1) & 7);
+    const int qn = (lane & 1) | ((lane >> 4) << 1);
     // A1 offset of this thread's rows (s, A, n2 = 4 qn .. 4 qn + 3) at K element n1
     const uint32_t a1_off = (uint32_t)((qn & 1) * 8 + (n1 & 7) * 16 + (s * 8 + (qn >> 1)) * SBO +
                                        (n1 >> 3) * LBO);
@@ -207,10 +207,14 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         wi[ix][1] = u.y;
       }
     }
-    PairSeq in{(int64_t)blockIdx.x, 0};
+    float2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
+    PairSeq in{(int64_t)blockIdx.x, 0}, de{(int64_t)blockIdx.x, 0};
     bool ok = true;
-    for (int64_t P = 0; P < total && ok; ++P) {
-      {
+    for (int64_t P = 0; P < total + 2 && ok; ++P) {
+      if (P < total) {
         // ---------------- input stage of pair P
         const int b = (int)(P & 1), r = (int)(P % R);
         const uint32_t u = (uint32_t)(P >> 1);
@@ -261,8 +265,6 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
 #pragma unroll
             for (int c = 0; c < 2; ++c) o[A][c][0] = o[A][c][1] = 0u;
         }
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(bars + RAWE + r);   // raw stage r may be refilled
         unsigned char* dst = a1 + b * TILE + a1_off;
 #pragma unroll
         for (int A = 0; A < 4; ++A)
@@ -274,24 +276,57 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         if (lane == 0) tc::mbar_arrive(bars + A1F + b);
         in.next(npairs);
       }
+      if (P >= 2) {
+        // ---------------- detection of pair P - 2: |X|^2 of both snapshots
+        const int64_t Pd = P - 2;
+        const int b = (int)(Pd & 1);
+        const uint32_t u = (uint32_t)(Pd >> 1);
+        if (!wait_warp(D2F + b, u & 1)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 128 + 64 * b;
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          uint32_t v[32];
+          tc::tmem_ld32(taddr + 32 * ss, v);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 x = make_float2(__uint_as_float(v[2 * k2]), __uint_as_float(v[2 * k2 + 1]));
+            acc[k2] = __ffma2_rn(x, x, acc[k2]);
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(bars + D2E + b);
+        if (de.q == npairs - 1) {
+          // last pair of the window: beams[item][A = warp][k1 = lane + 32 k2]
+          float* dst = a.beams + de.item * (int64_t)(4 * 512) + warp * 512 + lane;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            dst[32 * k2] = (acc[k2].x + acc[k2].y) * inv_s2;
+            acc[k2] = make_float2(0.f, 0.f);
+          }
+        }
+        de.next(npairs);
+      }
     }
   } else if (warp < 8) {
     // ============================================ stage-1 drain: twiddle, A2 (pair P)
     const int m = tid - 128;                          // TMEM row (s, A, n2)
     const int s = m >> 6, A = (m >> 4) & 3, n2 = m & 15;
     const int lq = warp - 4;
-    // twiddles W512^(n2 k1) of this row: half2 pairs over adjacent k1, by chunks of 8 k1
-    const uint4* tw4 = reinterpret_cast<const uint4*>(smem + L.tw) + n2 * 8;
+    // twiddles W512^(n2 k1) of this row: half2 pairs over adjacent k1 (cos, then -sin)
+    uint32_t ch[16], dh[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      ch[j] = ta.tw16[(n2 * 16 + j) * 2];
+      dh[j] = ta.tw16[(n2 * 16 + j) * 2 + 1];
+    }
     // A2 offset of element (m2 = A 32 + k1, k = n2) for k1 = 0 and the real part
     const uint32_t a2_off = (uint32_t)((n2 & 7) * 16 + (4 * A) * SBO + (n2 >> 3) * LBO + s * TILE);
-    float2 acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
-    const float inv_s2 = 1.0f / (ta.scale * ta.scale);
-    PairSeq de{(int64_t)blockIdx.x, 0};
     bool ok = true;
-    for (int64_t P = 0; P < total + 2 && ok; ++P) {
-      if (P < total) {
+    for (int64_t P = 0; P < total && ok; ++P) {
+      {
         const int b = (int)(P & 1);
         const uint32_t u = (uint32_t)(P >> 1);
         if (!wait_warp(D1F + b, u & 1)) { ok = false; break; }
@@ -313,15 +348,13 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
 #pragma unroll
           for (int qq = 0; qq < 2; ++qq) {                      // k1 = 8q .. 8q + 7
             const int q = 2 * hh + qq;
-            const uint4 cq = tw4[2 * q], dq = tw4[2 * q + 1];
-            const uint32_t cv[4] = {cq.x, cq.y, cq.z, cq.w}, dv[4] = {dq.x, dq.y, dq.z, dq.w};
             uint32_t tr[4], ti[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-              const int jl = 4 * qq + jj;
+              const int jl = 4 * qq + jj, j = 4 * q + jj;
               const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
               const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
-              const __half2 c = as_h2(cv[jj]), d = as_h2(dv[jj]);
+              const __half2 c = as_h2(ch[j]), d = as_h2(dh[j]);
               tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
               ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
             }
@@ -333,46 +366,11 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(bars + A2F + b);
       }
-      if (P >= 2) {
-        // ---------------- detection of pair P - 2: |X|^2 of both snapshots
-        const int64_t Pd = P - 2;
-        const int b = (int)(Pd & 1);
-        const uint32_t u = (uint32_t)(Pd >> 1);
-        if (!wait_warp(D2F + b, u & 1)) { ok = false; break; }
-        tc::fence_after_sync();
-        const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 128 + 64 * b;
-#pragma unroll
-        for (int ss = 0; ss < 2; ++ss) {
-          uint32_t v[32];
-          tc::tmem_ld32(taddr + 32 * ss, v);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            const float2 x = make_float2(__uint_as_float(v[2 * k2]), __uint_as_float(v[2 * k2 + 1]));
-            acc[k2] = __ffma2_rn(x, x, acc[k2]);
-          }
-        }
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(bars + D2E + b);
-        if (de.q == npairs - 1) {
-          // last pair of the window: beams[item][A = lq][k1 = lane + 32 k2]
-          float* dst = a.beams + de.item * (int64_t)(4 * 512) + lq * 512 + lane;
-#pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            dst[32 * k2] = (acc[k2].x + acc[k2].y) * inv_s2;
-            acc[k2] = make_float2(0.f, 0.f);
-          }
-        }
-        de.next(npairs);
-      }
     }
-  } else if (lane == 0) {
-    // ============================================ copies and MMAs (one thread)
+  } else if (warp == 8 && lane == 0) {
+    // ============================================ stage-1 MMAs and raw-byte copies
     const uint32_t id1 = tc::idesc_f16(128, 64, false) | (1u << 15);   // A MN-major
-    const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);
-    const uint32_t sa1 = tc::smem_u32(a1), sa2 = tc::smem_u32(a2);
-    const uint32_t sb1 = tc::smem_u32(smem + L.b1), sb2 = tc::smem_u32(smem + L.b2);
+    const uint32_t sa1 = tc::smem_u32(a1), sb1 = tc::smem_u32(smem + L.b1);
     // raw-byte source of the next pair to copy: the item's first byte is found once per
     // item (one 64-bit division), pairs then advance by a constant stride
     PairSeq cp{(int64_t)blockIdx.x, 0};
@@ -380,8 +378,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     const int64_t tstride = (int64_t)a.nfreq * a.npol * NANT;      // one time sample
     const bool two_pol = a.npol == 2;
     int64_t issued = 0;                                // pairs whose bytes were requested
-    auto copy = [&](int64_t P) {
-      const int r = (int)(P % R);
+    auto copy = [&]() {
+      const int r = (int)(issued % R);
       unsigned char* dst = raw + r * 2 * NANT;
       const int g = 2 * cp.q;
       const uint8_t* s0 = two_pol ? ibase + (int64_t)cp.q * tstride : ibase + snap_offset(a, g, NANT);
@@ -404,87 +402,31 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       }
       ++issued;
     };
-    // MMA descriptors of every buffer (constant for the launch)
-    uint64_t da1[2][2], da2[2][2][2], db1[2], db2[2];
+    uint64_t da1[2][2], db1[2];
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       db1[kk] = tc::smem_desc(sb1 + kk * 2 * B_LBO, B_LBO, B_SBO);
-      db2[kk] = tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO);
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        da1[b][kk] = tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO);
-#pragma unroll
-        for (int ss = 0; ss < 2; ++ss)
-          da2[b][ss][kk] = tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO);
-      }
+      for (int b = 0; b < 2; ++b) da1[b][kk] = tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO);
     }
-    // Event loop: whichever of the next MMA1, the next refill and the next MMA2 has its
-    // inputs ready is issued (non-blocking tests), so that no stream waits behind another.
-    while (issued < total && issued < R) copy(issued);
-    int64_t mma1 = 0, mma2 = 0;                        // MMAs issued
-    uint64_t t_idle = 0;
-    uint32_t idle = 0;
-    while (mma2 < total) {
-      bool prog = false;
-      if (mma1 < total) {
-        const int b = (int)(mma1 & 1);
-        const uint32_t u = (uint32_t)(mma1 >> 1);
-        if (tc::mbar_test(bars + A1F + b, u & 1) && (u == 0 || tc::mbar_test(bars + D1E + b, (u - 1) & 1))) {
-          tc::fence_after_sync();
-          if (b == 0) {
-            tc::mma_f16(tbase, da1[0][0], db1[0], id1, 0);
-            tc::mma_f16(tbase, da1[0][1], db1[1], id1, 1);
-          } else {
-            tc::mma_f16(tbase + 64, da1[1][0], db1[0], id1, 0);
-            tc::mma_f16(tbase + 64, da1[1][1], db1[1], id1, 1);
-          }
-          tc::mma_commit(bars + D1F + b);
-          tc::mma_commit(bars + A1E + b);
-          ++mma1;
-          prog = true;
-        }
+    while (issued < total && issued < R) copy();
+    int64_t mma1 = 0;
+    for (; mma1 < total; ++mma1) {
+      const int b = (int)(mma1 & 1);
+      const uint32_t u = (uint32_t)(mma1 >> 1);
+      if (!wait_sleep(A1F + b, u & 1) || (u >= 1 && !wait_sleep(D1E + b, (u - 1) & 1))) break;
+      tc::fence_after_sync();
+      if (b == 0) {
+        tc::mma_f16(tbase, da1[0][0], db1[0], id1, 0);
+        tc::mma_f16(tbase, da1[0][1], db1[1], id1, 1);
+      } else {
+        tc::mma_f16(tbase + 64, da1[1][0], db1[0], id1, 0);
+        tc::mma_f16(tbase + 64, da1[1][1], db1[1], id1, 1);
       }
-      // refill the raw stage that pair `issued - R` has been read from
-      if (issued < total && tc::mbar_test(bars + RAWE + (int)(issued % R), (uint32_t)(((issued / R) - 1) & 1))) {
-        copy(issued);
-        prog = true;
-      }
-      if (mma2 < mma1) {
-        const int b = (int)(mma2 & 1);
-        const uint32_t u = (uint32_t)(mma2 >> 1);
-        if (tc::mbar_test(bars + A2F + b, u & 1) && (u == 0 || tc::mbar_test(bars + D2E + b, (u - 1) & 1))) {
-          tc::fence_after_sync();
-          if (b == 0) {
-#pragma unroll
-            for (int ss = 0; ss < 2; ++ss) {
-              tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
-              tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
-            }
-          } else {
-#pragma unroll
-            for (int ss = 0; ss < 2; ++ss) {
-              tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
-              tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
-            }
-          }
-          tc::mma_commit(bars + D2F + b);
-          tc::mma_commit(bars + A2E + b);
-          ++mma2;
-          prog = true;
-        }
-      }
-      if (prog) {
-        idle = 0;
-        continue;
-      }
-      // nothing ready: back off briefly; give up after one second without progress
-      __nanosleep(32);
-      if ((++idle & 63) == 0) {
-        if (*abort_sm) break;
-        const uint64_t t = tc::globaltimer_ns();
-        if (idle == 64) t_idle = t;
-        else if (t - t_idle > WAIT_NS) { fail(); break; }
-      }
+      tc::mma_commit(bars + D1F + b);
+      tc::mma_commit(bars + A1E + b);
+      // every input warp read pair mma1's raw stage before its A1F arrival: refill it
+      if (issued < total) copy();
     }
     // Every copy and MMA issued must have landed before the CTA frees its memory. On the
     // normal path the other roles already waited for all of them; after a timeout, wait
@@ -492,6 +434,42 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     for (int64_t k = issued - 1; k >= 0 && k >= issued - R; --k)
       tc::mbar_wait(bars + RAWF + (int)(k % R), (uint32_t)((k / R) & 1), WAIT_NS);
     if (mma1 > 0) tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & 1), (uint32_t)(((mma1 - 1) >> 1) & 1), WAIT_NS);
+  } else if (warp == 9 && lane == 0) {
+    // ============================================ stage-2 MMAs
+    const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);   // A MN-major
+    const uint32_t sa2 = tc::smem_u32(a2), sb2 = tc::smem_u32(smem + L.b2);
+    uint64_t da2[2][2][2], db2[2];
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      db2[kk] = tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO);
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss)
+          da2[b][ss][kk] = tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO);
+    }
+    int64_t mma2 = 0;
+    for (; mma2 < total; ++mma2) {
+      const int b = (int)(mma2 & 1);
+      const uint32_t u = (uint32_t)(mma2 >> 1);
+      if (!wait_sleep(A2F + b, u & 1) || (u >= 1 && !wait_sleep(D2E + b, (u - 1) & 1))) break;
+      tc::fence_after_sync();
+      if (b == 0) {
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
+          tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
+        }
+      } else {
+#pragma unroll
+        for (int ss = 0; ss < 2; ++ss) {
+          tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
+          tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
+        }
+      }
+      tc::mma_commit(bars + D2F + b);
+      tc::mma_commit(bars + A2E + b);
+    }
     if (mma2 > 0) tc::mbar_wait(bars + D2F + (int)((mma2 - 1) & 1), (uint32_t)(((mma2 - 1) >> 1) & 1), WAIT_NS);
   }
   __syncwarp();

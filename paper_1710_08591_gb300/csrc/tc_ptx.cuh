@@ -145,6 +145,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// Wait (bounded by limit_ns of device time, and by *abort) for the phase with parity
+// `parity` of `bar`, suspending the thread between checks (try_wait with a suspend-time
+// hint of 20 us) instead of spinning, so that a waiting warp takes no issue slots.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                volatile int* abort) {
+  const uint32_t a = smem_u32(bar);
+  {
+    // fast path: the phase has usually completed already (non-blocking test)
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "r"(20000u)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    const uint64_t t = globaltimer_ns();
+    if (i == 0) t0 = t;
+    else if (t - t0 > limit_ns) return false;
+  }
+}
+
 // Non-blocking test: true if the phase with parity `parity` of `bar` has completed.
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

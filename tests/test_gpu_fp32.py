@@ -217,15 +217,20 @@ def test_tied_rejects_off_grid_pointing():
 @pytest.mark.parametrize("shape,prec", [((4, 256, 4, 512, 2, 2, 32, 16), "fp32"),
                                         ((3, 128, 3, 256, 2, 2, 32, 16), "fp32"),
                                         ((8, 64, 8, 128, 2, 2, 32, 16), "fp32"),
-                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16_serial"),
                                         ((4, 256, 4, 512, 2, 2, 32, 16), "tc_bf16"),
                                         ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16x3")])
-def test_misaligned_voltages_give_identical_beams(shape, prec):
+def test_misaligned_voltages_give_identical_beams(shape, prec, monkeypatch):
     """A voltage pointer off the 16-byte boundary is accepted (staged byte by byte instead
     of with 16-byte copies) and gives bit-identical beams. The aligned call runs the
     constant-size instance of the 4x256 lattice (or of an exactly 2x-padded warp-path
     shape), the misaligned one the runtime-size instance, so this also checks that both
-    sum in the same order."""
+    sum in the same order. (tc_fp16_serial: the serial tensor-core kernel, which serves
+    misaligned FP16 calls; aligned FP16 calls run the warp-specialised kernel, checked
+    against the oracle in test_misaligned_fp16_tensor_core_kernels_agree.)"""
+    if prec == "tc_fp16_serial":
+        monkeypatch.setenv("FFTBF_TC_KERNEL", "serial")
+        prec = "tc_fp16"
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=77)
     flat = torch.from_numpy(np.ascontiguousarray(v).reshape(-1))
@@ -243,3 +248,29 @@ def test_misaligned_voltages_give_identical_beams(shape, prec):
         outs.append(out.cpu().numpy())
     assert np.all(np.isfinite(outs[0]))
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_misaligned_fp16_tensor_core_kernels_agree():
+    """FP16 on the 4x256 lattice: an aligned voltage pointer runs the warp-specialised
+    tensor-core kernel (bulk copies need 16-byte alignment), a misaligned one the serial
+    kernel. Their roundings differ, so both are held to the FP16 form's bound against the
+    oracle (5e-3 of each beam) and to each other."""
+    shape = (4, 256, 4, 512, 2, 2, 32, 16)
+    nx, ny, mx, my, npol, nfreq, T, n_int = shape
+    v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=78)
+    ref = oracle_beams(v, w, nx, ny, mx, my, npol, nfreq, n_int)
+    flat = torch.from_numpy(np.ascontiguousarray(v).reshape(-1))
+    base = torch.zeros(flat.numel() + 16, dtype=torch.uint8, device="cuda")
+    outs = []
+    for off in (0, 3):
+        base[off:off + flat.numel()].copy_(flat)
+        out = torch.full((T // n_int, nfreq, mx, my), float("nan"), device="cuda")
+        with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
+            fb.plan_set_precision(plan, fb.PREC_TC_FP16)
+            fb.execute(plan, base[off:off + flat.numel()], T, out)
+            fb.plan_sync(plan)
+        outs.append(out.cpu().numpy())
+    for o in outs:
+        assert np.all(np.isfinite(o))
+        assert (np.abs(o - ref) / ref).max() <= 5e-3
+    assert (np.abs(outs[0] - outs[1]) / ref).max() <= 1e-2
