@@ -27,8 +27,13 @@
 namespace fftbf {
 
 // ---------------------------------------------------------------- complex helpers --
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Packed two-lane FP32 (add / fma .f32x2 of sm_100 and later): one instruction per complex
+// add; a - b as fma(b, -1, a), which rounds exactly as the subtraction does, so the sums are
+// bit-identical to scalar code while taking half the issue slots.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -57,12 +62,15 @@ template <> struct Dft<2> {
 };
 template <> struct Dft<4> {
   __device__ __forceinline__ static void run(float2* v) {
+    // d = v1 - v3; v1' = d02 - i d = d02 + (d.y, -d.x), v3' = d02 + (-d.y, d.x): one fma
+    // each on the swapped pair (d.y, d.x), exact multiplies by +-1
     float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    float2 s13 = cadd(v[1], v[3]), d13 = mul_mi(csub(v[1], v[3]));
+    float2 s13 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    const float2 dsw = make_float2(d.y, d.x);
     v[0] = cadd(s02, s13);
     v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13);
-    v[3] = csub(d02, d13);
+    v[1] = __ffma2_rn(dsw, make_float2(1.f, -1.f), d02);
+    v[3] = __ffma2_rn(dsw, make_float2(-1.f, 1.f), d02);
   }
 };
 constexpr float kRs2 = 0.70710678118654752440f;

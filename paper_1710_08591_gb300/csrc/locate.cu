@@ -80,10 +80,35 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double warp_sum_d(double v) {
+// Compensated FP32 summation (Neumaier): s + c carries the sum of the added terms with an
+// error of about one rounding of the result, independent of the number of terms.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+};
+// Error-free sum of two floats (Knuth's TwoSum): a + b = t + e exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float* e) {
+  const float t = a + b;
+  const float bp = t - a;
+  *e = (a - (t - bp)) + (b - bp);
+  return t;
+}
+// Warp sum of compensated partial sums: every level adds exactly (TwoSum) and keeps the
+// rounding errors in the compensation term.
+__device__ __forceinline__ float warp_sum_c(CSum v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, v.s, o);
+    const float oc = __shfl_xor_sync(0xffffffffu, v.c, o);
+    float e;
+    v.s = two_sum(v.s, os, &e);
+    v.c = (v.c + oc) + e;
+  }
+  return v.s + v.c;
 }
 
 // advance a position by dy (in units of y) and renormalise fr into [0, 1), ih into [0, M)
@@ -175,7 +200,9 @@ __global__ void __launch_bounds__(32 * kLocWarps, 4) localise_kernel(
       if (axy.fit) move(axy, &ihy, &fry, Dy * axy.newton / T * (float)my);
     }
     // the pointed beam at the estimate, from every FFT beam: sum_B w^B sum_A w^A P[A, B]
-    double T = 0.0;
+    // (regridding weights of both signs: compensated FP32 sums keep the cancellation exact
+    // to about one rounding)
+    CSum T;
     if (axx.fit) {
       for (int c = 0; c < mx; c += kLocTaps) {
         for (int t = lane; t < kLocTaps && c + t < mx; t += 32) {
@@ -191,7 +218,7 @@ __global__ void __launch_bounds__(32 * kLocWarps, 4) localise_kernel(
           else if (B != b0) continue;
           float s = 0.f;
           for (int A = 0; A < na; ++A) s = fmaf(wx[A], tile[(c + A) * my + B], s);
-          T += (double)(wB * s);
+          T.add(wB * s);
         }
         __syncwarp();
       }
@@ -200,14 +227,14 @@ __global__ void __launch_bounds__(32 * kLocWarps, 4) localise_kernel(
         float wB = 1.f, d;
         if (axy.fit) dir_weight(axy, ihy, fry, B, &wB, &d);
         else if (B != b0) continue;
-        T += (double)(wB * tile[a0 * my + B]);
+        T.add(wB * tile[a0 * my + B]);
       }
     }
-    T = warp_sum_d(T);
+    const float Tsum = warp_sum_c(T);
     if (lane == 0) {
-      out[3 * item] = (float)(((double)ihx + (double)frx) / (double)mx);
-      out[3 * item + 1] = (float)(((double)ihy + (double)fry) / (double)my);
-      out[3 * item + 2] = (float)T;
+      out[3 * item] = fmaf(frx, axx.invM, (float)ihx * axx.invM);
+      out[3 * item + 1] = fmaf(fry, axy.invM, (float)ihy * axy.invM);
+      out[3 * item + 2] = Tsum;
     }
   }
 }
