@@ -68,7 +68,10 @@ def flops_per_snapshot(nx, ny, mx, my):
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_FP32 = 16 * (403.262208e6 + 3.753472e6)
+TRAFFIC_FP32 = None
+# The beam kernel each tensor-core form launches on the 4x256 lattice
+TC_KERNEL = {"tc_fp16": "beams_tcw_kernel<true>", "tc_bf16": "beams_tc_kernel<1, 0, 1>",
+             "tc_fp16x3": "beams_tc_kernel<0, 1, 1>"}
 # The same for one batched step (one batch_kernel launch over 8192 samples), from the
 # 512-sample profile case (`--workload batched --profile-case`) scaled x16.
 TRAFFIC_BATCH = 16 * (2184.420e6 + 36.285184e6)
@@ -389,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
                "the same rate); the beam kernel runs inside a seconds-long step")
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_pk, "unit": "TFLOP/s",
             "frac": achieved / fp32_pk, "traffic": TRAFFIC_FP32,
-            "kernel": "beams_fp32_n512_kernel<4, true>", "ms_per_launch": k_ms,
+            "kernel": "beams_fp32_4x256_kernel<true>", "ms_per_launch": k_ms,
             "flops_per_snapshot": FLOPS_PER_SNAPSHOT,
             "peak_source": "measured: " + fp32["source"],
             "fp32_probe": fp32,
@@ -404,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
         rate = samples_launch / (k_ms / 1e3)
         tfl = TC_FLOPS_SPEC * rate / 1e12
         roof = {"bound": "tensor", "achieved": tfl, "peak": tpk, "unit": "TFLOP/s",
-                "frac": tfl / tpk, "traffic": None, "kernel": "beams_tc_kernel",
+                "frac": tfl / tpk, "traffic": None, "kernel": TC_KERNEL[args.form],
                 "ms_per_launch": k_ms, "flops_per_sample": TC_FLOPS_SPEC, "peak_source": tpk_src,
                 "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
                         "peak_gbs": peaks["hbm_gbs"],
@@ -454,7 +457,7 @@ def run_ours(args, rank, world, local_rank):
                 "value": samples_per_step() * world / (fms / 1e3), "ms_per_step": fms,
                 "beam_ms_per_launch": b_ms, "beam_antenna_samples_per_s": rate,
                 "roofline": {
-                    "kernel": "beams_tc_kernel", "bound": "tensor", "ms_per_launch": b_ms,
+                    "kernel": TC_KERNEL[form], "bound": "tensor", "ms_per_launch": b_ms,
                     "timing": "CUDA events around each beam launch on its stream",
                     "tensor_as_specified": {"flops_per_sample": TC_FLOPS_SPEC, "achieved": spec,
                                             "peak": tpk, "unit": "TFLOP/s", "frac": spec / tpk,

@@ -14,6 +14,9 @@
 // each warp then transforms its own region. Two CTA barriers per iteration; the
 // transforms synchronise only within their warp. Accumulation order is fixed per work
 // item, as in the generic kernel.
+// The 4x256 lattice with 16-byte aligned voltages runs the same arithmetic, in the same
+// order, in its own kernel (beam_fp32_4x256.cu); this one serves the other shapes and
+// unaligned voltages.
 #include <cuda_runtime.h>
 
 #include "beam_fp32.cuh"
@@ -33,18 +36,16 @@ __device__ __forceinline__ int in_slot(int iy) { return (iy & 15) + kRow * (iy >
 #define FFTBF_N512_MIN_BLOCKS (24 / FFTBF_N512_NW)   // CTAs per SM the register budget targets
 #endif
 
-// NY256: 256 N-S feeds in every row, all of them live, E-W axis a plain MX-point DFT and
-// 16-byte aligned voltages (the feed offsets of the input stage become constants).
-template <int MX, bool NY256 = false>
+template <int MX>
 __global__ void __launch_bounds__((MX > 4 ? MX : FFTBF_N512_NW) * 32, MX > 4 ? 2 : FFTBF_N512_MIN_BLOCKS)
 beams_fp32_n512_kernel(const BeamArgs a) {
   constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;   // warps per CTA = transforms per iteration
   constexpr int S = NW / MX;                // snapshots per iteration
   constexpr int NT = NW * 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int ny = NY256 ? 256 : a.ny;
-  const int nyf = NY256 ? 256 : a.nyf;
-  const int nant = NY256 ? MX * 256 : a.nx * a.ny;
+  const int ny = a.ny;
+  const int nyf = a.nyf;
+  const int nant = a.nx * a.ny;
   const int rawsz = (S * nant + 15) & ~15;
   // tables and regions first, so the weights start 16-byte aligned (128-bit loads)
   float2* tw512 = reinterpret_cast<float2*>(smem + 2 * rawsz);  // [32 k1][16 n2] = W512^(n2 k1)
@@ -57,8 +58,7 @@ beams_fp32_n512_kernel(const BeamArgs a) {
   const int nsnap = a.n_int * a.npol;
   const int niter = (nsnap + S - 1) / S;
   const int64_t nitems = a.nwin * a.nfreq;
-  const bool vec16 =
-      NY256 || (((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0));
+  const bool vec16 = ((nant & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.volts) & 15) == 0);
 
   for (int i = threadIdx.x; i < nant; i += NT) wsm[i] = a.w[i];
   for (int i = threadIdx.x; i < MX * a.nx; i += NT) exsm[i] = a.ex[i];
@@ -114,72 +114,42 @@ beams_fp32_n512_kernel(const BeamArgs a) {
 
     // ---- unpack x weight, E-W transform -> Z[s*MX + A][in_slot(iy)]
     const uint8_t* raw = smem + cur * rawsz;
-    if constexpr (NY256) {
-      // one snapshot, two adjacent feeds per thread: 16-bit byte loads and 128-bit weight
-      // loads
-      static_assert(MX == 4 && S == 1 && 2 * NT == 256, "one feed pair per thread");
-      const int iy = 2 * threadIdx.x;
-      float2 z0[4], z1[4];
+    for (int c = threadIdx.x; c < S * 256; c += NT) {
+      const int s = c >> 8, iy = c & 255;
+      float2 z[MX];
 #pragma unroll
-      for (int ix = 0; ix < 4; ++ix) {
-        const unsigned v = *reinterpret_cast<const uint16_t*>(raw + ix * 256 + iy);
-        const float4 w = *reinterpret_cast<const float4*>(wsm + ix * 256 + iy);
-        const float2 x0 = unpack_byte(v & 255u), x1 = unpack_byte(v >> 8);
-        if (a.real_w) {
-          // real weights: two multiplies (the roundings of the complex product)
-          z0[ix] = make_float2(w.x * x0.x, w.x * x0.y);
-          z1[ix] = make_float2(w.z * x1.x, w.z * x1.y);
-        } else {
-          z0[ix] = cmul(make_float2(w.x, w.y), x0);
-          z1[ix] = cmul(make_float2(w.z, w.w), x1);
-        }
-      }
-      Dft<4>::run(z0);
-      Dft<4>::run(z1);
-      const int sl = n512::in_slot(iy);      // iy + 1 is the next slot (iy even)
+      for (int A = 0; A < MX; ++A) z[A] = czero();
+      if (iy < nyf && it * S + s < nsnap) {
+        const uint8_t* rs = raw + s * nant;
+        if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
+          if (a.ew_dft) {
+            if (a.real_w) {
+              // real weights: w x in two multiplies (the same roundings as the complex
+              // product with a zero imaginary part)
 #pragma unroll
-      for (int A = 0; A < 4; ++A) {
-        reg[A * n512::kRegion + sl] = z0[A];
-        reg[A * n512::kRegion + sl + 1] = z1[A];
-      }
-    } else {
-      for (int c = threadIdx.x; c < S * 256; c += NT) {
-        const int s = c >> 8, iy = c & 255;
-        float2 z[MX];
-#pragma unroll
-        for (int A = 0; A < MX; ++A) z[A] = czero();
-        if (iy < nyf && it * S + s < nsnap) {
-          const uint8_t* rs = raw + s * nant;
-          if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
-            if (a.ew_dft) {
-              if (a.real_w) {
-                // real weights: w x in two multiplies (the same roundings as the complex
-                // product with a zero imaginary part)
-#pragma unroll
-                for (int ix = 0; ix < MX; ++ix) {
-                  const float wr = wsm[ix * ny + iy].x;
-                  const float2 xv = unpack_byte(rs[ix * ny + iy]);
-                  z[ix] = make_float2(wr * xv.x, wr * xv.y);
-                }
-              } else {
-#pragma unroll
-                for (int ix = 0; ix < MX; ++ix)
-                  z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
+              for (int ix = 0; ix < MX; ++ix) {
+                const float wr = wsm[ix * ny + iy].x;
+                const float2 xv = unpack_byte(rs[ix * ny + iy]);
+                z[ix] = make_float2(wr * xv.x, wr * xv.y);
               }
-              Dft<MX>::run(z);
-            }
-          }
-          if (!a.ew_dft) {
-            for (int ix = 0; ix < a.nx; ++ix) {
-              const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
+            } else {
 #pragma unroll
-              for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
+              for (int ix = 0; ix < MX; ++ix)
+                z[ix] = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
             }
+            Dft<MX>::run(z);
           }
         }
+        if (!a.ew_dft) {
+          for (int ix = 0; ix < a.nx; ++ix) {
+            const float2 col = cmul(wsm[ix * ny + iy], unpack_byte(rs[ix * ny + iy]));
 #pragma unroll
-        for (int A = 0; A < MX; ++A) reg[(s * MX + A) * n512::kRegion + n512::in_slot(iy)] = z[A];
+            for (int A = 0; A < MX; ++A) z[A] = cadd(z[A], cmul(exsm[A * a.nx + ix], col));
+          }
+        }
       }
+#pragma unroll
+      for (int A = 0; A < MX; ++A) reg[(s * MX + A) * n512::kRegion + n512::in_slot(iy)] = z[A];
     }
     __syncthreads();                                  // (B) regions written
 
@@ -247,12 +217,12 @@ static size_t n512_smem_bytes(const BeamArgs& a, int S, int NW) {
 
 template <int MX>
 static int launch_n512_mx(const BeamArgs& a, int nsm, cudaStream_t st) {
+  // the 4x256 lattice with aligned voltages has its own kernel (beam_fp32_4x256.cu)
+  if (MX == 4 && fp32_4x256_eligible(a)) return launch_beams_fp32_4x256(a, nsm, st);
   constexpr int NW = MX > 4 ? MX : FFTBF_N512_NW;
   constexpr int S = NW / MX;
   const size_t smem = n512_smem_bytes(a, S, NW);
-  const bool ny256 = MX == 4 && a.ew_dft && a.nx == MX && a.ny == 256 && a.nyf == 256 &&
-                     (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
-  auto kern = ny256 ? beams_fp32_n512_kernel<MX, MX == 4> : beams_fp32_n512_kernel<MX>;
+  auto kern = beams_fp32_n512_kernel<MX>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));

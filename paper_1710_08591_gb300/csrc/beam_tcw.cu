@@ -16,9 +16,9 @@
 //     writes 8 bytes per (E-W beam, component);
 //   * the stage-1 drain packs two adjacent k1 (adjacent stage-2 rows) into one half2 and
 //     writes 16 bytes per (component, 8 k1) instead of one 4-byte value per k1.
-// The B operands (DFT matrices) stay K-major. Stage-1 outputs are planar along N (real
-// parts of k1 0..31, then imaginary parts), stage-2 outputs interleaved (re, im) per k2, so
-// that the detector squares both parts of a beam with one packed FFMA2.
+// The B operands (DFT matrices) stay K-major. Both stages' outputs are planar along N (real
+// parts, then imaginary parts), so that the detector squares two adjacent beams k2, k2 + 1
+// with one packed FFMA2 per component into one float2 accumulator.
 //
 // Unpacking: a voltage byte (bits 7..4 real, 3..0 imaginary, two's complement) is decoded
 // exactly into FP16 by placing the real nibble in the mantissa of 1024 (ulp 1, nibble four
@@ -27,14 +27,20 @@
 // factor 16 is folded into the FP16 weights (w / 16, a power of two, so the products
 // round as w x would).
 //
+// Tensor memory holds a ring of four 64-column buffers: buffer t = P % 4 receives pair P's
+// stage-1 result D1 (columns re k1, im k1), and, once the drain has read it, stage 2
+// writes the pair's D2 (32 columns per snapshot) over the same columns; the detector frees
+// the buffer for pair P + 4. Four pairs are thus in flight between stage 1 and detection.
+//
 // Roles (10 warps, 320 threads, two CTAs per SM by tensor memory: 256 columns each):
-//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-2
-//              (D2[(P-2)%2] -> registers), lane quarter = warp;
-//   warps 4-7  stage-1 drain of pair P (D1[P%2] -> twiddle -> A2[P%2]), lane quarter = warp-4;
-//   warp 8     one thread: MMA1(P) once A1[P%2] is written and D1[P%2] drained, then the
-//              bulk copy of pair P+R's raw bytes into the ring stage pair P was read from
-//              (2 KB per pair, R stages);
-//   warp 9     one thread: MMA2(P) once A2[P%2] is written and D2[P%2] detected.
+//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-3
+//              (D2 in buffer (P-3)%4 -> registers), lane quarter = warp;
+//   warps 4-7  stage-1 drain of pair P (D1 in buffer P%4 -> twiddle -> A2[P%2]), lane
+//              quarter = warp-4;
+//   warp 8     one thread: MMA1(P) once A1[P%2] is written and buffer P%4 detected, then
+//              the bulk copy of pair P+R's raw bytes into the ring stage pair P was read
+//              from (2 KB per pair, R stages);
+//   warp 9     one thread: MMA2(P) once A2[P%2] is written and D1 of buffer P%4 drained.
 // Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Waiting threads
 // are suspended (try_wait with a suspend-time hint) rather than spinning, so waiting warps
 // take no issue slots. Every wait is bounded by one second of device time; on timeout the
@@ -53,13 +59,15 @@ namespace tcw {
 constexpr int NT = 320;
 constexpr int R = 8;                          // raw-byte ring stages (2 KB each)
 constexpr int NANT = 1024;                    // feeds of the 4x256 lattice
-constexpr uint32_t TMEM_COLS = 256;           // D1[2] at 0, 64; D2[2] at 128, 192
+constexpr int NT4 = 4;                        // tensor-memory ring: pairs in flight
+constexpr uint32_t TMEM_COLS = 64 * NT4;      // buffer t at columns 64 t: D1 of a pair, then
+                                              // its D2 (stage 2 overwrites the drained D1)
 // MN-major operand tiles (128 rows x 32 K, 16-bit): element (m, k) at
 //   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
 constexpr int SBO = 128, LBO = 2048, TILE = 8192;
 constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
-enum { RAWF = 0, A1F = RAWF + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + 2,
-       A2F = D1E + 2, A2E = A2F + 2, D2F = A2E + 2, D2E = D2F + 2, NBAR = D2E + 2 };
+enum { RAWF = 0, A1F = RAWF + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
+       A2F = D1E + NT4, A2E = A2F + 2, D2F = A2E + 2, D2E = D2F + NT4, NBAR = D2E + NT4 };
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 struct Smem {
@@ -132,8 +140,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
   if (tid == 0) {
     for (int i = 0; i < NBAR; ++i) {
       uint32_t c = 4;                                  // one arrival per warp of a role
-      if ((i >= RAWF && i < RAWF + R) || (i >= A1E && i < A1E + 2) || (i >= D1F && i < D1F + 2) ||
-          (i >= A2E && i < A2E + 2) || (i >= D2F && i < D2F + 2))
+      if ((i >= RAWF && i < RAWF + R) || (i >= A1E && i < A1E + 2) || (i >= D1F && i < D1F + NT4) ||
+          (i >= A2E && i < A2E + 2) || (i >= D2F && i < D2F + NT4))
         c = 1;                                         // expect_tx arrival or MMA commit
       tc::mbar_init(bars + i, c);
     }
@@ -207,13 +215,14 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         wi[ix][1] = u.y;
       }
     }
-    float2 acc[16];
+    float2 acc[8];                                    // |X|^2 sums of k2 = 2p, 2p + 1
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 8; ++i) acc[i] = make_float2(0.f, 0.f);
     const float inv_s2 = 1.0f / (ta.scale * ta.scale);
     PairSeq in{(int64_t)blockIdx.x, 0}, de{(int64_t)blockIdx.x, 0};
     bool ok = true;
-    for (int64_t P = 0; P < total + 2 && ok; ++P) {
+    constexpr int LAG = NT4 - 1;                      // detection lags the input by LAG pairs
+    for (int64_t P = 0; P < total + LAG && ok; ++P) {
       if (P < total) {
         // ---------------- input stage of pair P
         const int b = (int)(P & 1), r = (int)(P % R);
@@ -276,35 +285,37 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
         if (lane == 0) tc::mbar_arrive(bars + A1F + b);
         in.next(npairs);
       }
-      if (P >= 2) {
-        // ---------------- detection of pair P - 2: |X|^2 of both snapshots
-        const int64_t Pd = P - 2;
-        const int b = (int)(Pd & 1);
-        const uint32_t u = (uint32_t)(Pd >> 1);
-        if (!wait_warp(D2F + b, u & 1)) { ok = false; break; }
+      if (P >= LAG) {
+        // ---------------- detection of pair P - LAG: |X|^2 of both snapshots
+        const int64_t Pd = P - LAG;
+        const int t4 = (int)(Pd & (NT4 - 1));
+        const uint32_t u = (uint32_t)(Pd / NT4);
+        if (!wait_warp(D2F + t4, u & 1)) { ok = false; break; }
         tc::fence_after_sync();
-        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 128 + 64 * b;
+        const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 64 * t4;
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss) {
-          uint32_t v[32];
+          uint32_t v[32];                                  // re of k2 0..15, then im
           tc::tmem_ld32(taddr + 32 * ss, v);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            const float2 x = make_float2(__uint_as_float(v[2 * k2]), __uint_as_float(v[2 * k2 + 1]));
-            acc[k2] = __ffma2_rn(x, x, acc[k2]);
+          for (int p = 0; p < 8; ++p) {
+            const float2 xr = make_float2(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
+            const float2 xi = make_float2(__uint_as_float(v[16 + 2 * p]), __uint_as_float(v[17 + 2 * p]));
+            acc[p] = __ffma2_rn(xi, xi, __ffma2_rn(xr, xr, acc[p]));
           }
         }
         tc::fence_before_sync();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(bars + D2E + b);
+        if (lane == 0) tc::mbar_arrive(bars + D2E + t4);     // buffer t4 is free
         if (de.q == npairs - 1) {
           // last pair of the window: beams[item][A = warp][k1 = lane + 32 k2]
           float* dst = a.beams + de.item * (int64_t)(4 * 512) + warp * 512 + lane;
 #pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            dst[32 * k2] = (acc[k2].x + acc[k2].y) * inv_s2;
-            acc[k2] = make_float2(0.f, 0.f);
+          for (int p = 0; p < 8; ++p) {
+            dst[64 * p] = acc[p].x * inv_s2;
+            dst[64 * p + 32] = acc[p].y * inv_s2;
+            acc[p] = make_float2(0.f, 0.f);
           }
         }
         de.next(npairs);
@@ -329,10 +340,11 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       {
         const int b = (int)(P & 1);
         const uint32_t u = (uint32_t)(P >> 1);
-        if (!wait_warp(D1F + b, u & 1)) { ok = false; break; }
+        const int t4 = (int)(P & (NT4 - 1));
+        if (!wait_warp(D1F + t4, (uint32_t)((P / NT4) & 1))) { ok = false; break; }
         if (u >= 1 && !wait_warp(A2E + b, (u - 1) & 1)) { ok = false; break; }
         tc::fence_after_sync();
-        const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 64 * b;
+        const uint32_t taddr = tbase + ((uint32_t)(32 * lq) << 16) + 64 * t4;
         unsigned char* dst = a2 + 2 * b * TILE + a2_off;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {                        // k1 = 16 hh .. 16 hh + 15
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
           if (hh == 1) {
             tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(bars + D1E + b);     // D1[b] may be overwritten
+            if (lane == 0) tc::mbar_arrive(bars + D1E + t4);    // D2 may overwrite D1
           }
 #pragma unroll
           for (int qq = 0; qq < 2; ++qq) {                      // k1 = 8q .. 8q + 7
@@ -414,16 +426,18 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     for (; mma1 < total; ++mma1) {
       const int b = (int)(mma1 & 1);
       const uint32_t u = (uint32_t)(mma1 >> 1);
-      if (!wait_sleep(A1F + b, u & 1) || (u >= 1 && !wait_sleep(D1E + b, (u - 1) & 1))) break;
+      const int t4 = (int)(mma1 & (NT4 - 1));
+      const uint32_t u4 = (uint32_t)(mma1 / NT4);
+      if (!wait_sleep(A1F + b, u & 1) || (u4 >= 1 && !wait_sleep(D2E + t4, (u4 - 1) & 1))) break;
       tc::fence_after_sync();
       if (b == 0) {
-        tc::mma_f16(tbase, da1[0][0], db1[0], id1, 0);
-        tc::mma_f16(tbase, da1[0][1], db1[1], id1, 1);
+        tc::mma_f16(tbase + 64 * t4, da1[0][0], db1[0], id1, 0);
+        tc::mma_f16(tbase + 64 * t4, da1[0][1], db1[1], id1, 1);
       } else {
-        tc::mma_f16(tbase + 64, da1[1][0], db1[0], id1, 0);
-        tc::mma_f16(tbase + 64, da1[1][1], db1[1], id1, 1);
+        tc::mma_f16(tbase + 64 * t4, da1[1][0], db1[0], id1, 0);
+        tc::mma_f16(tbase + 64 * t4, da1[1][1], db1[1], id1, 1);
       }
-      tc::mma_commit(bars + D1F + b);
+      tc::mma_commit(bars + D1F + t4);
       tc::mma_commit(bars + A1E + b);
       // every input warp read pair mma1's raw stage before its A1F arrival: refill it
       if (issued < total) copy();
@@ -433,7 +447,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     // here (bounded, regardless of the abort flag) for the last ones of each ring.
     for (int64_t k = issued - 1; k >= 0 && k >= issued - R; --k)
       tc::mbar_wait(bars + RAWF + (int)(k % R), (uint32_t)((k / R) & 1), WAIT_NS);
-    if (mma1 > 0) tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & 1), (uint32_t)(((mma1 - 1) >> 1) & 1), WAIT_NS);
+    if (mma1 > 0)
+      tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & (NT4 - 1)), (uint32_t)(((mma1 - 1) / NT4) & 1), WAIT_NS);
   } else if (warp == 9 && lane == 0) {
     // ============================================ stage-2 MMAs
     const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);   // A MN-major
@@ -452,25 +467,28 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     for (; mma2 < total; ++mma2) {
       const int b = (int)(mma2 & 1);
       const uint32_t u = (uint32_t)(mma2 >> 1);
-      if (!wait_sleep(A2F + b, u & 1) || (u >= 1 && !wait_sleep(D2E + b, (u - 1) & 1))) break;
+      const int t4 = (int)(mma2 & (NT4 - 1));
+      const uint32_t u4 = (uint32_t)(mma2 / NT4);
+      if (!wait_sleep(A2F + b, u & 1) || !wait_sleep(D1E + t4, u4 & 1)) break;
       tc::fence_after_sync();
       if (b == 0) {
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss) {
-          tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
-          tc::mma_f16(tbase + 128 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
+          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
+          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
         }
       } else {
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss) {
-          tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
-          tc::mma_f16(tbase + 192 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
+          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
+          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
         }
       }
-      tc::mma_commit(bars + D2F + b);
+      tc::mma_commit(bars + D2F + t4);
       tc::mma_commit(bars + A2E + b);
     }
-    if (mma2 > 0) tc::mbar_wait(bars + D2F + (int)((mma2 - 1) & 1), (uint32_t)(((mma2 - 1) >> 1) & 1), WAIT_NS);
+    if (mma2 > 0)
+      tc::mbar_wait(bars + D2F + (int)((mma2 - 1) & (NT4 - 1)), (uint32_t)(((mma2 - 1) / NT4) & 1), WAIT_NS);
   }
   __syncwarp();
   tc::fence_before_sync();
@@ -492,14 +510,16 @@ int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st) {
   if (items <= 0) return FFTBF_OK;
   const tcw::Smem L = tcw::layout();
   // two CTAs per SM (256 of the 512 tensor-memory columns each): keep a third from
-  // fitting by shared memory as well
+  // fitting by shared memory as well, as it could not allocate tensor memory until one of
+  // the others exits
   size_t smem = (size_t)L.total;
   if (smem < 77 * 1024) smem = 77 * 1024;
   auto kern = a.real_w ? beams_tcw_kernel<true> : beams_tcw_kernel<false>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));
-  const int64_t grid = items < (int64_t)nsm * 2 ? items : (int64_t)nsm * 2;
+  const int64_t per_wave = (int64_t)nsm * 2;
+  const int64_t grid = items < per_wave ? items : per_wave;
   kern<<<(unsigned)grid, tcw::NT, smem, st>>>(ta);
   FFTBF_CUDA_TRY(cudaGetLastError());
   return FFTBF_OK;
@@ -509,7 +529,7 @@ int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st) {
 // Stage matrices of the warp-specialised FP16 form, row-major [n][k] (n = output, k =
 // input), FP64 rounded once to FP16, and the W512 twiddle pairs:
 //   b1[n = co 32 + k1][k = ci 16 + n1]   W32^(n1 k1), planar in and out
-//   b2[n = 2 k2 + co][k = ci 16 + n2]    W16^(n2 k2), planar in, interleaved out
+//   b2[n = co 16 + k2][k = ci 16 + n2]   W16^(n2 k2), planar in and out
 //   tw16[(n2 16 + j) 2 + {0, 1}]         (cos, cos) and (-sin, -sin) of 2 pi n2 k1 / 512 for
 //                                        k1 = 2j, 2j + 1, as half2
 // With W = C + iS (S = -sin): out_re = sum in_re C - in_im S, out_im = sum in_re S + in_im C.
@@ -532,7 +552,7 @@ __global__ void tcw_tables_kernel(uint16_t* b1, uint16_t* b2, uint32_t* tw16) {
   }
   if (i < 32 * 32) {
     const int n = i >> 5, k = i & 31;
-    const int k2 = n >> 1, co = n & 1, ci = k >> 4, n2 = k & 15;
+    const int k2 = n & 15, co = n >> 4, ci = k >> 4, n2 = k & 15;
     double sn, cs;
     sincospi(2.0 * ((n2 * k2) % 16) / 16.0, &sn, &cs);
     b2[i] = h(entry(co, ci, cs, -sn));

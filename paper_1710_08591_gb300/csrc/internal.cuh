@@ -64,6 +64,8 @@ bool fp32_fft_supported(int mx, int my);
 // Warp-per-transform kernel for my == 512 with at most 256 feeds on the N-S axis.
 bool fp32_n512_supported(const BeamArgs& a);
 int launch_beams_fp32_n512(const BeamArgs& a, int nsm, cudaStream_t st);
+bool fp32_4x256_eligible(const BeamArgs& a);
+int launch_beams_fp32_4x256(const BeamArgs& a, int nsm, cudaStream_t st);
 int launch_debug_unpack(const uint8_t* in, int64_t n, float* out, cudaStream_t st);
 
 // Batched launches (batch.cu): one job = one plan's buffers over nwin windows.
