@@ -33,14 +33,20 @@
 // the buffer for pair P + 4. Four pairs are thus in flight between stage 1 and detection.
 //
 // Roles (10 warps, 320 threads, two CTAs per SM by tensor memory: 256 columns each):
-//   warps 0-3  input stage of pair P (bytes -> A1[P%2]) and detection of pair P-3
-//              (D2 in buffer (P-3)%4 -> registers), lane quarter = warp;
+//   warps 0-3  rounds of two pairs: the input stage of pairs 2k, 2k+1 (bytes -> A1 tiles
+//              P%4), then detection of pairs 2k-3, 2k-2 (D2 in buffers P%4 -> registers),
+//              lane quarter = warp; one wait for the round's raw bytes, one for its A1
+//              tiles, one arrival when both are written, one wait before detecting;
 //   warps 4-7  stage-1 drain of pair P (D1 in buffer P%4 -> twiddle -> A2[P%2]), lane
 //              quarter = warp-4;
-//   warp 8     one thread: MMA1(P) once A1[P%2] is written and buffer P%4 detected, then
-//              the bulk copy of pair P+R's raw bytes into the ring stage pair P was read
-//              from (2 KB per pair, R stages);
+//   warp 8     one thread: MMA1 of both pairs of round k once their A1 tiles are written
+//              (each pair once its buffer is detected), then the bulk copies of round
+//              k+RQ's raw bytes into the ring stages round k was read from (2 KB per pair,
+//              both pairs counted on one barrier);
 //   warp 9     one thread: MMA2(P) once A2[P%2] is written and D1 of buffer P%4 drained.
+// Synchronisation, not arithmetic, paces this pipeline: each wait or arrival costs a few
+// hundred cycles of latency under load, so the input role, which has the most of them per
+// pair, does its waits and arrivals once per two pairs.
 // Hand-offs are mbarriers (one elected arrival per warp after __syncwarp). Waiting threads
 // are suspended (try_wait with a suspend-time hint) rather than spinning, so waiting warps
 // take no issue slots. Every wait is bounded by one second of device time; on timeout the
@@ -57,7 +63,9 @@ namespace fftbf {
 
 namespace tcw {
 constexpr int NT = 320;
-constexpr int R = 8;                          // raw-byte ring stages (2 KB each)
+constexpr int NA2 = 2;                        // stage-2 operand tile pairs (pairs in flight)
+constexpr int R = 8;                          // raw-byte ring stages (2 KB each, one pair)
+constexpr int RQ = R / 2;                     // ... filled and waited for two pairs at a time
 constexpr int NANT = 1024;                    // feeds of the 4x256 lattice
 constexpr int NT4 = 4;                        // tensor-memory ring: pairs in flight
 constexpr uint32_t TMEM_COLS = 64 * NT4;      // buffer t at columns 64 t: D1 of a pair, then
@@ -66,8 +74,10 @@ constexpr uint32_t TMEM_COLS = 64 * NT4;      // buffer t at columns 64 t: D1 of
 //   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
 constexpr int SBO = 128, LBO = 2048, TILE = 8192;
 constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
-enum { RAWF = 0, A1F = RAWF + R, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
-       A2F = D1E + NT4, A2E = A2F + 2, D2F = A2E + 2, D2E = D2F + NT4, NBAR = D2E + NT4 };
+// RAWF per round stage; A1F, A1E per round parity (a round's two pairs use A1 tiles
+// 2 (k % 2), + 1); D1F, D1E, D2F, D2E per tensor-memory buffer; A2F, A2E per A2 tile pair
+enum { RAWF = 0, A1F = RAWF + RQ, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
+       A2F = D1E + NT4, A2E = A2F + NA2, D2F = A2E + NA2, D2E = D2F + NT4, NBAR = D2E + NT4 };
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 struct Smem {
@@ -77,8 +87,8 @@ __host__ __device__ inline Smem layout() {
   Smem L;
   int o = 0;
   auto take = [&](int bytes) { int r = o; o += (bytes + 127) & ~127; return r; };
-  L.a1 = take(2 * TILE);                 // A1[b]
-  L.a2 = take(4 * TILE);                 // A2[b][s]
+  L.a1 = take(4 * TILE);                 // A1[pair % 4]
+  L.a2 = take(2 * NA2 * TILE);           // A2[b][s]
   L.b1 = take(64 * 32 * 2);
   L.b2 = take(32 * 32 * 2);
   L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
@@ -140,8 +150,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
   if (tid == 0) {
     for (int i = 0; i < NBAR; ++i) {
       uint32_t c = 4;                                  // one arrival per warp of a role
-      if ((i >= RAWF && i < RAWF + R) || (i >= A1E && i < A1E + 2) || (i >= D1F && i < D1F + NT4) ||
-          (i >= A2E && i < A2E + 2) || (i >= D2F && i < D2F + NT4))
+      if ((i >= RAWF && i < RAWF + RQ) || (i >= A1E && i < A1E + 2) || (i >= D1F && i < D1F + NT4) ||
+          (i >= A2E && i < A2E + NA2) || (i >= D2F && i < D2F + NT4))
         c = 1;                                         // expect_tx arrival or MMA commit
       tc::mbar_init(bars + i, c);
     }
@@ -221,77 +231,86 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     const float inv_s2 = 1.0f / (ta.scale * ta.scale);
     PairSeq in{(int64_t)blockIdx.x, 0}, de{(int64_t)blockIdx.x, 0};
     bool ok = true;
-    constexpr int LAG = NT4 - 1;                      // detection lags the input by LAG pairs
-    for (int64_t P = 0; P < total + LAG && ok; ++P) {
-      if (P < total) {
-        // ---------------- input stage of pair P
-        const int b = (int)(P & 1), r = (int)(P % R);
-        const uint32_t u = (uint32_t)(P >> 1);
-        if (!wait_warp(RAWF + r, (uint32_t)((P / R) & 1))) { ok = false; break; }
-        if (u >= 1 && !wait_warp(A1E + b, (u - 1) & 1)) { ok = false; break; }
-        const bool valid = s == 0 || 2 * in.q + 1 < nsnap;
-        uint32_t o[4][2][2];                               // [A][re, im][n2 pair]
-        if (valid) {
-          uint32_t word[4];
+    // round k: the input stage of pairs 2k and 2k + 1 (one raw-byte wait, one A1 wait and
+    // one A1F arrival for both), then detection of pairs 2k - 3 and 2k - 2 (one D2F wait, on
+    // the later pair: its stage-2 MMAs were committed after the earlier pair's)
+    const int64_t nround = (total + 1) / 2;
+    for (int64_t k = 0; k < nround + 2 && ok; ++k) {
+      if (k < nround) {
+        const int ab = (int)(k & 1);
+        if (!wait_warp(RAWF + (int)(k % RQ), (uint32_t)((k / RQ) & 1))) { ok = false; break; }
+        if (k >= 2 && !wait_warp(A1E + ab, (uint32_t)(((k >> 1) - 1) & 1))) { ok = false; break; }
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+          const int64_t P = 2 * k + j;
+          if (P >= total) break;
+          const int r = (int)(P % R), b = (int)(P & 3);   // raw stage, A1 tile
+          const bool valid = s == 0 || 2 * in.q + 1 < nsnap;
+          uint32_t o[4][2][2];                               // [A][re, im][n2 pair]
+          if (valid) {
+            uint32_t word[4];
 #pragma unroll
-          for (int ix = 0; ix < 4; ++ix)
-            word[ix] = *reinterpret_cast<const uint32_t*>(raw + r * 2 * NANT + s * NANT + ix * 256 + feed0);
+            for (int ix = 0; ix < 4; ++ix)
+              word[ix] = *reinterpret_cast<const uint32_t*>(raw + r * 2 * NANT + s * NANT + ix * 256 + feed0);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            __half2 zr[4], zi[4];
+            for (int h = 0; h < 2; ++h) {
+              __half2 zr[4], zi[4];
 #pragma unroll
-            for (int ix = 0; ix < 4; ++ix) {
-              // bytes of feeds n2 = 4 qn + 2h, + 1 beside 0x64 bytes: [0x64 b1 0x64 b0]
-              const uint32_t t = __byte_perm(word[ix], 0x64646464u, h ? 0x4342u : 0x4140u);
-              const __half2 re = __hsub2(as_h2((t & 0xFFF0FFF0u) ^ 0x00800080u), as_h2(0x64806480u));
-              const __half2 im = __hsub2(as_h2((t & 0x000F000Fu) ^ 0x74087408u), as_h2(0x74087408u));
-              if constexpr (REALW) {
-                zr[ix] = __hmul2_rn(re, as_h2(wr[ix][h]));
-                zi[ix] = __hmul2_rn(im, as_h2(wr[ix][h]));
-              } else {
-                const __half2 w_r = as_h2(wr[ix][h]), w_i = as_h2(wi[ix][h]);
-                zr[ix] = __hfma2(__hneg2(im), w_i, __hmul2_rn(re, w_r));
-                zi[ix] = __hfma2(im, w_r, __hmul2_rn(re, w_i));
+              for (int ix = 0; ix < 4; ++ix) {
+                // bytes of feeds n2 = 4 qn + 2h, + 1 beside 0x64 bytes: [0x64 b1 0x64 b0]
+                const uint32_t t = __byte_perm(word[ix], 0x64646464u, h ? 0x4342u : 0x4140u);
+                const __half2 re = __hsub2(as_h2((t & 0xFFF0FFF0u) ^ 0x00800080u), as_h2(0x64806480u));
+                const __half2 im = __hsub2(as_h2((t & 0x000F000Fu) ^ 0x74087408u), as_h2(0x74087408u));
+                if constexpr (REALW) {
+                  zr[ix] = __hmul2_rn(re, as_h2(wr[ix][h]));
+                  zi[ix] = __hmul2_rn(im, as_h2(wr[ix][h]));
+                } else {
+                  const __half2 w_r = as_h2(wr[ix][h]), w_i = as_h2(wi[ix][h]);
+                  zr[ix] = __hfma2(__hneg2(im), w_i, __hmul2_rn(re, w_r));
+                  zi[ix] = __hfma2(im, w_r, __hmul2_rn(re, w_i));
+                }
               }
+              // 4-point E-W DFT, Y_A = sum_ix z_ix (-i)^(A ix), planar
+              const __half2 ar = __hadd2(zr[0], zr[2]), ai = __hadd2(zi[0], zi[2]);
+              const __half2 br = __hsub2(zr[0], zr[2]), bi = __hsub2(zi[0], zi[2]);
+              const __half2 cr = __hadd2(zr[1], zr[3]), ci = __hadd2(zi[1], zi[3]);
+              const __half2 dr = __hsub2(zr[1], zr[3]), di = __hsub2(zi[1], zi[3]);
+              o[0][0][h] = as_u(__hadd2(ar, cr));
+              o[0][1][h] = as_u(__hadd2(ai, ci));
+              o[2][0][h] = as_u(__hsub2(ar, cr));
+              o[2][1][h] = as_u(__hsub2(ai, ci));
+              o[1][0][h] = as_u(__hadd2(br, di));            // b - i d
+              o[1][1][h] = as_u(__hsub2(bi, dr));
+              o[3][0][h] = as_u(__hsub2(br, di));            // b + i d
+              o[3][1][h] = as_u(__hadd2(bi, dr));
             }
-            // 4-point E-W DFT, Y_A = sum_ix z_ix (-i)^(A ix), planar
-            const __half2 ar = __hadd2(zr[0], zr[2]), ai = __hadd2(zi[0], zi[2]);
-            const __half2 br = __hsub2(zr[0], zr[2]), bi = __hsub2(zi[0], zi[2]);
-            const __half2 cr = __hadd2(zr[1], zr[3]), ci = __hadd2(zi[1], zi[3]);
-            const __half2 dr = __hsub2(zr[1], zr[3]), di = __hsub2(zi[1], zi[3]);
-            o[0][0][h] = as_u(__hadd2(ar, cr));
-            o[0][1][h] = as_u(__hadd2(ai, ci));
-            o[2][0][h] = as_u(__hsub2(ar, cr));
-            o[2][1][h] = as_u(__hsub2(ai, ci));
-            o[1][0][h] = as_u(__hadd2(br, di));            // b - i d
-            o[1][1][h] = as_u(__hsub2(bi, dr));
-            o[3][0][h] = as_u(__hsub2(br, di));            // b + i d
-            o[3][1][h] = as_u(__hadd2(bi, dr));
+          } else {
+#pragma unroll
+            for (int A = 0; A < 4; ++A)
+#pragma unroll
+              for (int c = 0; c < 2; ++c) o[A][c][0] = o[A][c][1] = 0u;
           }
-        } else {
+          unsigned char* dst = a1 + b * TILE + a1_off;
 #pragma unroll
           for (int A = 0; A < 4; ++A)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) o[A][c][0] = o[A][c][1] = 0u;
+            for (int c = 0; c < 2; ++c)
+              *reinterpret_cast<uint2*>(dst + A * 2 * SBO + c * 2 * LBO) = make_uint2(o[A][c][0], o[A][c][1]);
+          in.next(npairs);
         }
-        unsigned char* dst = a1 + b * TILE + a1_off;
-#pragma unroll
-        for (int A = 0; A < 4; ++A)
-#pragma unroll
-          for (int c = 0; c < 2; ++c)
-            *reinterpret_cast<uint2*>(dst + A * 2 * SBO + c * 2 * LBO) = make_uint2(o[A][c][0], o[A][c][1]);
         tc::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(bars + A1F + b);
-        in.next(npairs);
+        if (lane == 0) tc::mbar_arrive(bars + A1F + ab);
       }
-      if (P >= LAG) {
-        // ---------------- detection of pair P - LAG: |X|^2 of both snapshots
-        const int64_t Pd = P - LAG;
+      // ---------------- detection of pairs 2k - 3 .. min(2k - 2, total - 1)
+      const int64_t p0 = 2 * k - 3 > 0 ? 2 * k - 3 : 0;
+      const int64_t p1 = 2 * k - 2 < total - 1 ? 2 * k - 2 : total - 1;
+      if (p1 < p0) continue;
+      if (!wait_warp(D2F + (int)(p1 & (NT4 - 1)), (uint32_t)((p1 / NT4) & 1))) { ok = false; break; }
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int64_t Pd = p0; Pd <= p1; ++Pd) {
         const int t4 = (int)(Pd & (NT4 - 1));
-        const uint32_t u = (uint32_t)(Pd / NT4);
-        if (!wait_warp(D2F + t4, u & 1)) { ok = false; break; }
-        tc::fence_after_sync();
         const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + 64 * t4;
 #pragma unroll
         for (int ss = 0; ss < 2; ++ss) {
@@ -338,8 +357,8 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     bool ok = true;
     for (int64_t P = 0; P < total && ok; ++P) {
       {
-        const int b = (int)(P & 1);
-        const uint32_t u = (uint32_t)(P >> 1);
+        const int b = (int)(P % NA2);
+        const uint32_t u = (uint32_t)(P / NA2);
         const int t4 = (int)(P & (NT4 - 1));
         if (!wait_warp(D1F + t4, (uint32_t)((P / NT4) & 1))) { ok = false; break; }
         if (u >= 1 && !wait_warp(A2E + b, (u - 1) & 1)) { ok = false; break; }
@@ -389,100 +408,102 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     const uint8_t* ibase = item_volts(a, cp.item, NANT);
     const int64_t tstride = (int64_t)a.nfreq * a.npol * NANT;      // one time sample
     const bool two_pol = a.npol == 2;
-    int64_t issued = 0;                                // pairs whose bytes were requested
-    auto copy = [&]() {
-      const int r = (int)(issued % R);
-      unsigned char* dst = raw + r * 2 * NANT;
+    // the bytes of the pair cp points at (1 KB if it is the lone last snapshot of an odd
+    // count), copied to dst and counted on bar; then cp moves on
+    auto pair_bytes = [&](int q) -> uint32_t { return 2 * q + 1 < nsnap ? 2 * NANT : NANT; };
+    auto copy_pair = [&](unsigned char* dst, uint64_t* bar) {
       const int g = 2 * cp.q;
       const uint8_t* s0 = two_pol ? ibase + (int64_t)cp.q * tstride : ibase + snap_offset(a, g, NANT);
       if (g + 1 < nsnap) {
-        tc::mbar_arrive_expect_tx(bars + RAWF + r, 2 * NANT);
         if (two_pol) {
-          tc::bulk_g2s(dst, s0, 2 * NANT, bars + RAWF + r);
+          tc::bulk_g2s(dst, s0, 2 * NANT, bar);
         } else {
-          tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
-          tc::bulk_g2s(dst + NANT, ibase + snap_offset(a, g + 1, NANT), NANT, bars + RAWF + r);
+          tc::bulk_g2s(dst, s0, NANT, bar);
+          tc::bulk_g2s(dst + NANT, ibase + snap_offset(a, g + 1, NANT), NANT, bar);
         }
       } else {
-        tc::mbar_arrive_expect_tx(bars + RAWF + r, NANT);
-        tc::bulk_g2s(dst, s0, NANT, bars + RAWF + r);
+        tc::bulk_g2s(dst, s0, NANT, bar);
       }
       if (++cp.q == npairs) {
         cp.q = 0;
         cp.item += gridDim.x;
         if (cp.item < nitems) ibase = item_volts(a, cp.item, NANT);
       }
+    };
+    const int64_t nround = (total + 1) / 2;
+    int64_t issued = 0;                                // rounds whose bytes were requested
+    // round `issued` (pairs 2 issued, + 1) into raw stages 2 (issued % RQ), + 1, on one barrier
+    auto copy_round = [&]() {
+      const int rq = (int)(issued % RQ);
+      uint64_t* bar = bars + RAWF + rq;
+      unsigned char* dst = raw + rq * 4 * NANT;
+      const bool two = 2 * issued + 1 < total;
+      const uint32_t bytes = pair_bytes(cp.q) + (two ? pair_bytes(cp.q + 1 == npairs ? 0 : cp.q + 1) : 0);
+      tc::mbar_arrive_expect_tx(bar, bytes);
+      copy_pair(dst, bar);
+      if (two) copy_pair(dst + 2 * NANT, bar);
       ++issued;
     };
-    uint64_t da1[2][2], db1[2];
+    // descriptors of tile 0; tile b starts b TILE bytes further (the start-address field
+    // holds the address / 16)
+    uint64_t da1[2], db1[2];
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       db1[kk] = tc::smem_desc(sb1 + kk * 2 * B_LBO, B_LBO, B_SBO);
-#pragma unroll
-      for (int b = 0; b < 2; ++b) da1[b][kk] = tc::smem_desc(sa1 + b * TILE + kk * 2 * LBO, LBO, SBO);
+      da1[kk] = tc::smem_desc(sa1 + kk * 2 * LBO, LBO, SBO);
     }
-    while (issued < total && issued < R) copy();
-    int64_t mma1 = 0;
-    for (; mma1 < total; ++mma1) {
-      const int b = (int)(mma1 & 1);
-      const uint32_t u = (uint32_t)(mma1 >> 1);
-      const int t4 = (int)(mma1 & (NT4 - 1));
-      const uint32_t u4 = (uint32_t)(mma1 / NT4);
-      if (!wait_sleep(A1F + b, u & 1) || (u4 >= 1 && !wait_sleep(D2E + t4, (u4 - 1) & 1))) break;
-      tc::fence_after_sync();
-      if (b == 0) {
-        tc::mma_f16(tbase + 64 * t4, da1[0][0], db1[0], id1, 0);
-        tc::mma_f16(tbase + 64 * t4, da1[0][1], db1[1], id1, 1);
-      } else {
-        tc::mma_f16(tbase + 64 * t4, da1[1][0], db1[0], id1, 0);
-        tc::mma_f16(tbase + 64 * t4, da1[1][1], db1[1], id1, 1);
+    while (issued < nround && issued < RQ) copy_round();
+    int64_t mma1 = 0;                                  // pairs whose MMAs were issued
+    bool ok = true;
+    for (int64_t k = 0; k < nround && ok; ++k) {
+      const int ab = (int)(k & 1);
+      if (!wait_sleep(A1F + ab, (uint32_t)((k >> 1) & 1))) break;
+      for (int j = 0; j < 2 && mma1 < total; ++j, ++mma1) {
+        const int t4 = (int)(mma1 & (NT4 - 1));
+        const uint32_t u4 = (uint32_t)(mma1 / NT4);
+        if (u4 >= 1 && !wait_sleep(D2E + t4, (u4 - 1) & 1)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint64_t off = (uint64_t)(((int)(mma1 & 3) * TILE) >> 4);   // A1 tile mma1 % 4
+        tc::mma_f16(tbase + 64 * t4, da1[0] + off, db1[0], id1, 0);
+        tc::mma_f16(tbase + 64 * t4, da1[1] + off, db1[1], id1, 1);
+        tc::mma_commit(bars + D1F + t4);
       }
-      tc::mma_commit(bars + D1F + t4);
-      tc::mma_commit(bars + A1E + b);
-      // every input warp read pair mma1's raw stage before its A1F arrival: refill it
-      if (issued < total) copy();
+      if (!ok) break;
+      tc::mma_commit(bars + A1E + ab);
+      // every input warp read round k's raw stages before its A1F arrival: refill them
+      if (issued < nround) copy_round();
     }
     // Every copy and MMA issued must have landed before the CTA frees its memory. On the
     // normal path the other roles already waited for all of them; after a timeout, wait
     // here (bounded, regardless of the abort flag) for the last ones of each ring.
-    for (int64_t k = issued - 1; k >= 0 && k >= issued - R; --k)
-      tc::mbar_wait(bars + RAWF + (int)(k % R), (uint32_t)((k / R) & 1), WAIT_NS);
+    for (int64_t k = issued - 1; k >= 0 && k >= issued - RQ; --k)
+      tc::mbar_wait(bars + RAWF + (int)(k % RQ), (uint32_t)((k / RQ) & 1), WAIT_NS);
     if (mma1 > 0)
       tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & (NT4 - 1)), (uint32_t)(((mma1 - 1) / NT4) & 1), WAIT_NS);
   } else if (warp == 9 && lane == 0) {
     // ============================================ stage-2 MMAs
     const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);   // A MN-major
     const uint32_t sa2 = tc::smem_u32(a2), sb2 = tc::smem_u32(smem + L.b2);
-    uint64_t da2[2][2][2], db2[2];
+    uint64_t da2[2][2], db2[2];                        // tile pair 0; pair b is 2 b TILE further
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       db2[kk] = tc::smem_desc(sb2 + kk * 2 * B_LBO, B_LBO, B_SBO);
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int ss = 0; ss < 2; ++ss)
-          da2[b][ss][kk] = tc::smem_desc(sa2 + (2 * b + ss) * TILE + kk * 2 * LBO, LBO, SBO);
+      for (int ss = 0; ss < 2; ++ss) da2[ss][kk] = tc::smem_desc(sa2 + ss * TILE + kk * 2 * LBO, LBO, SBO);
     }
     int64_t mma2 = 0;
     for (; mma2 < total; ++mma2) {
-      const int b = (int)(mma2 & 1);
-      const uint32_t u = (uint32_t)(mma2 >> 1);
+      const int b = (int)(mma2 % NA2);
+      const uint32_t u = (uint32_t)(mma2 / NA2);
       const int t4 = (int)(mma2 & (NT4 - 1));
       const uint32_t u4 = (uint32_t)(mma2 / NT4);
       if (!wait_sleep(A2F + b, u & 1) || !wait_sleep(D1E + t4, u4 & 1)) break;
       tc::fence_after_sync();
-      if (b == 0) {
+      const uint64_t off = (uint64_t)((2 * b * TILE) >> 4);
 #pragma unroll
-        for (int ss = 0; ss < 2; ++ss) {
-          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[0][ss][0], db2[0], id2, 0);
-          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[0][ss][1], db2[1], id2, 1);
-        }
-      } else {
-#pragma unroll
-        for (int ss = 0; ss < 2; ++ss) {
-          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[1][ss][0], db2[0], id2, 0);
-          tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[1][ss][1], db2[1], id2, 1);
-        }
+      for (int ss = 0; ss < 2; ++ss) {
+        tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[ss][0] + off, db2[0], id2, 0);
+        tc::mma_f16(tbase + 64 * t4 + 32 * ss, da2[ss][1] + off, db2[1], id2, 1);
       }
       tc::mma_commit(bars + D2F + t4);
       tc::mma_commit(bars + A2E + b);
