@@ -68,7 +68,9 @@ def flops_per_snapshot(nx, ny, mx, my):
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_FP32 = None
+TRAFFIC_FP32 = 16 * (403.222784e6 + 3.644416e6)
+# The same for the FP16 tensor-core form's beam kernel (`--profile-case --form tc_fp16`).
+TRAFFIC_TCW = 16 * (402.730240e6 + 6.111488e6)
 # The beam kernel each tensor-core form launches on the 4x256 lattice
 TC_KERNEL = {"tc_fp16": "beams_tcw_kernel<true>", "tc_bf16": "beams_tc_kernel<1, 0, 1>",
              "tc_fp16x3": "beams_tc_kernel<0, 1, 1>"}
@@ -407,7 +409,8 @@ def run_ours(args, rank, world, local_rank):
         rate = samples_launch / (k_ms / 1e3)
         tfl = TC_FLOPS_SPEC * rate / 1e12
         roof = {"bound": "tensor", "achieved": tfl, "peak": tpk, "unit": "TFLOP/s",
-                "frac": tfl / tpk, "traffic": None, "kernel": TC_KERNEL[args.form],
+                "frac": tfl / tpk, "traffic": TRAFFIC_TCW if args.form == "tc_fp16" else None,
+                "kernel": TC_KERNEL[args.form],
                 "ms_per_launch": k_ms, "flops_per_sample": TC_FLOPS_SPEC, "peak_source": tpk_src,
                 "hbm": {"achieved_gbs": bytes_launch / (k_ms / 1e3) / 1e9,
                         "peak_gbs": peaks["hbm_gbs"],
@@ -458,6 +461,7 @@ def run_ours(args, rank, world, local_rank):
                 "beam_ms_per_launch": b_ms, "beam_antenna_samples_per_s": rate,
                 "roofline": {
                     "kernel": TC_KERNEL[form], "bound": "tensor", "ms_per_launch": b_ms,
+                    "traffic": TRAFFIC_TCW if form == "tc_fp16" else None,
                     "timing": "CUDA events around each beam launch on its stream",
                     "tensor_as_specified": {"flops_per_sample": TC_FLOPS_SPEC, "achieved": spec,
                                             "peak": tpk, "unit": "TFLOP/s", "frac": spec / tpk,
