@@ -868,9 +868,9 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const BeamArgs& a = ta.b;
   if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
-  // FP16 on the 4x256 lattice: the warp-specialised kernel with MN-major planar operands
-  // (beam_tcw.cu) unless FFTBF_TC_KERNEL=serial or FFTBF_TC_PIPE=1 ask for the kernels
-  // below. Of those two, the serial kernel (several CTAs per SM, every warp in every phase)
+  // FP16 and BF16 on the 4x256 lattice: the warp-specialised kernel with MN-major planar
+  // operands (beam_tcw.cu) unless FFTBF_TC_KERNEL=serial or FFTBF_TC_PIPE=1 ask for the
+  // kernels below. Of those two, the serial kernel (several CTAs per SM, every warp in every phase)
   // measures faster than the first warp-specialised pipeline on the 4x256 lattice.
   const char* pipe = getenv("FFTBF_TC_PIPE");
   const char* which = getenv("FFTBF_TC_KERNEL");

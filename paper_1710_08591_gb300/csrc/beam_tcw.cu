@@ -1,6 +1,9 @@
-// Tensor-core FP16 form of the FFT-beam hot path on the 4x256 lattice (4 E-W beams x 512
-// N-S beams, Eq. fftbeamform with the N-S axis zero-padded to 2n, Eq. b2n-1), as a
-// warp-specialised pipeline.
+// Tensor-core FP16 and BF16 forms of the FFT-beam hot path on the 4x256 lattice (4 E-W
+// beams x 512 N-S beams, Eq. fftbeamform with the N-S axis zero-padded to 2n, Eq. b2n-1),
+// as a warp-specialised pipeline. The two forms share the input stage, computed in packed
+// half (the BF16 form rounds its results to BF16 as it stores the stage-1 operand), and
+// differ in the stage matrices, the MMA instruction descriptor and the twiddle: packed
+// half for FP16, FP32 rounded once to BF16 for BF16 (as the serial kernel does it).
 //
 // The 512-point N-S transform of each (snapshot, E-W beam) is split as 512 = 32 x 16
 // (n = n2 + 16 n1, k = k1 + 32 k2; inputs with n1 >= 16 are the padding):
@@ -53,6 +56,7 @@
 // CTA records FFTBF_ETIMEOUT, every role leaves its loop, the issuing threads wait
 // (bounded) for their copies and MMAs in flight, and the tensor memory is freed before
 // exit.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -74,6 +78,7 @@ constexpr uint32_t TMEM_COLS = 64 * NT4;      // buffer t at columns 64 t: D1 of
 //   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
 constexpr int SBO = 128, LBO = 2048, TILE = 8192;
 constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
+constexpr int TWF_ROW = 17;                   // float4 per n2 row of the FP32 twiddles (padded)
 // RAWF per round stage; A1F, A1E per round parity (a round's two pairs use A1 tiles
 // 2 (k % 2), + 1); D1F, D1E, D2F, D2E per tensor-memory buffer; A2F, A2E per A2 tile pair
 enum { RAWF = 0, A1F = RAWF + RQ, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
@@ -81,7 +86,7 @@ enum { RAWF = 0, A1F = RAWF + RQ, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
 constexpr uint64_t WAIT_NS = 1000000000ull;
 
 struct Smem {
-  int a1, a2, b1, b2, w, raw, bars, misc, total;
+  int a1, a2, b1, b2, w, twf, raw, bars, misc, total;
 };
 __host__ __device__ inline Smem layout() {
   Smem L;
@@ -92,6 +97,7 @@ __host__ __device__ inline Smem layout() {
   L.b1 = take(64 * 32 * 2);
   L.b2 = take(32 * 32 * 2);
   L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
+  L.twf = take(16 * TWF_ROW * 16);       // FP32 twiddles of the BF16 form
   L.raw = take(R * 2 * NANT);
   L.bars = take(NBAR * 8);
   L.misc = take(16);
@@ -104,6 +110,18 @@ namespace {
 
 __device__ __forceinline__ __half2 as_h2(uint32_t v) { return *reinterpret_cast<__half2*>(&v); }
 __device__ __forceinline__ uint32_t as_u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+// A stage-1 operand pair computed in packed half, as the form's operand type: itself for
+// FP16, rounded to BF16 for the BF16 form (the FP16 value carries 11 significant bits, so
+// this is the BF16 rounding of the exact value except within ~2^-12 of a BF16 boundary)
+template <bool BF16>
+__device__ __forceinline__ uint32_t operand(__half2 v) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 b = __float22bfloat162_rn(__half22float2(v));
+    return *reinterpret_cast<const uint32_t*>(&b);
+  } else {
+    return as_u(v);
+  }
+}
 
 // The CTA's sequence of (work item, snapshot pair): items blockIdx.x, + gridDim.x, ...
 struct PairSeq {
@@ -119,7 +137,7 @@ struct PairSeq {
 
 }  // namespace
 
-template <bool REALW>
+template <bool REALW, bool BF16>
 __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) {
   using namespace tcw;
   const BeamArgs& a = ta.b;
@@ -179,6 +197,15 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       const float2 w = a.w[i];
       w16[i] = __float2half_rn(w.x * sc);
       w16[NANT + i] = __float2half_rn(w.y * sc);
+    }
+    if constexpr (BF16) {
+      // (cos, cos, -sin, -sin) of W512^(n2 k1) for k1 = 2j, 2j + 1, from the plan's table
+      float4* tw = reinterpret_cast<float4*>(smem + L.twf);
+      for (int i = tid; i < 16 * 16; i += NT) {
+        const int r = i >> 4, j = i & 15;
+        const float2 w0 = a.tw[(r * 2 * j) & 511], w1 = a.tw[(r * (2 * j + 1)) & 511];
+        tw[r * TWF_ROW + j] = make_float4(w0.x, w1.x, w0.y, w1.y);
+      }
     }
   }
   tc::fence_proxy_async_smem();
@@ -275,14 +302,14 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
               const __half2 br = __hsub2(zr[0], zr[2]), bi = __hsub2(zi[0], zi[2]);
               const __half2 cr = __hadd2(zr[1], zr[3]), ci = __hadd2(zi[1], zi[3]);
               const __half2 dr = __hsub2(zr[1], zr[3]), di = __hsub2(zi[1], zi[3]);
-              o[0][0][h] = as_u(__hadd2(ar, cr));
-              o[0][1][h] = as_u(__hadd2(ai, ci));
-              o[2][0][h] = as_u(__hsub2(ar, cr));
-              o[2][1][h] = as_u(__hsub2(ai, ci));
-              o[1][0][h] = as_u(__hadd2(br, di));            // b - i d
-              o[1][1][h] = as_u(__hsub2(bi, dr));
-              o[3][0][h] = as_u(__hsub2(br, di));            // b + i d
-              o[3][1][h] = as_u(__hadd2(bi, dr));
+              o[0][0][h] = operand<BF16>(__hadd2(ar, cr));
+              o[0][1][h] = operand<BF16>(__hadd2(ai, ci));
+              o[2][0][h] = operand<BF16>(__hsub2(ar, cr));
+              o[2][1][h] = operand<BF16>(__hsub2(ai, ci));
+              o[1][0][h] = operand<BF16>(__hadd2(br, di));            // b - i d
+              o[1][1][h] = operand<BF16>(__hsub2(bi, dr));
+              o[3][0][h] = operand<BF16>(__hsub2(br, di));            // b + i d
+              o[3][1][h] = operand<BF16>(__hadd2(bi, dr));
             }
           } else {
 #pragma unroll
@@ -345,12 +372,17 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     const int m = tid - 128;                          // TMEM row (s, A, n2)
     const int s = m >> 6, A = (m >> 4) & 3, n2 = m & 15;
     const int lq = warp - 4;
-    // twiddles W512^(n2 k1) of this row: half2 pairs over adjacent k1 (cos, then -sin)
-    uint32_t ch[16], dh[16];
+    // twiddles W512^(n2 k1) of this row: FP16, half2 pairs over adjacent k1 (cos, then
+    // -sin), in registers; BF16, FP32 quadruples (cos, cos, -sin, -sin) in shared memory
+    // (the twiddle is applied in FP32 and the product rounded once to BF16)
+    uint32_t ch[BF16 ? 1 : 16], dh[BF16 ? 1 : 16];
+    const float4* twf = reinterpret_cast<const float4*>(smem + L.twf) + n2 * TWF_ROW;
+    if constexpr (!BF16) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      ch[j] = ta.tw16[(n2 * 16 + j) * 2];
-      dh[j] = ta.tw16[(n2 * 16 + j) * 2 + 1];
+      for (int j = 0; j < 16; ++j) {
+        ch[j] = ta.tw16[(n2 * 16 + j) * 2];
+        dh[j] = ta.tw16[(n2 * 16 + j) * 2 + 1];
+      }
     }
     // A2 offset of element (m2 = A 32 + k1, k = n2) for k1 = 0 and the real part
     const uint32_t a2_off = (uint32_t)((n2 & 7) * 16 + (4 * A) * SBO + (n2 >> 3) * LBO + s * TILE);
@@ -383,11 +415,23 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               const int jl = 4 * qq + jj, j = 4 * q + jj;
-              const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
-              const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
-              const __half2 c = as_h2(ch[j]), d = as_h2(dh[j]);
-              tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
-              ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
+              if constexpr (BF16) {
+                const float4 w = twf[j];
+                const float2 re = make_float2(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
+                const float2 im = make_float2(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
+                const float2 c = make_float2(w.x, w.y), d = make_float2(w.z, w.w);
+                const float2 yr = __ffma2_rn(re, c, __fmul2_rn(im, make_float2(-d.x, -d.y)));
+                const float2 yi = __ffma2_rn(re, d, __fmul2_rn(im, c));
+                const __nv_bfloat162 br = __float22bfloat162_rn(yr), bi = __float22bfloat162_rn(yi);
+                tr[jj] = *reinterpret_cast<const uint32_t*>(&br);
+                ti[jj] = *reinterpret_cast<const uint32_t*>(&bi);
+              } else {
+                const __half2 hr = __floats2half2_rn(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
+                const __half2 hi = __floats2half2_rn(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
+                const __half2 c = as_h2(ch[j]), d = as_h2(dh[j]);
+                tr[jj] = as_u(__hfma2(__hneg2(hi), d, __hmul2(hr, c)));   // re x c - im x d
+                ti[jj] = as_u(__hfma2(hi, c, __hmul2(hr, d)));            // re x d + im x c
+              }
             }
             *reinterpret_cast<uint4*>(dst + q * SBO) = make_uint4(tr[0], tr[1], tr[2], tr[3]);
             *reinterpret_cast<uint4*>(dst + q * SBO + 2 * LBO) = make_uint4(ti[0], ti[1], ti[2], ti[3]);
@@ -400,7 +444,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     }
   } else if (warp == 8 && lane == 0) {
     // ============================================ stage-1 MMAs and raw-byte copies
-    const uint32_t id1 = tc::idesc_f16(128, 64, false) | (1u << 15);   // A MN-major
+    const uint32_t id1 = tc::idesc_f16(128, 64, BF16) | (1u << 15);   // A MN-major
     const uint32_t sa1 = tc::smem_u32(a1), sb1 = tc::smem_u32(smem + L.b1);
     // raw-byte source of the next pair to copy: the item's first byte is found once per
     // item (one 64-bit division), pairs then advance by a constant stride
@@ -482,7 +526,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       tc::mbar_wait(bars + D1F + (int)((mma1 - 1) & (NT4 - 1)), (uint32_t)(((mma1 - 1) / NT4) & 1), WAIT_NS);
   } else if (warp == 9 && lane == 0) {
     // ============================================ stage-2 MMAs
-    const uint32_t id2 = tc::idesc_f16(128, 32, false) | (1u << 15);   // A MN-major
+    const uint32_t id2 = tc::idesc_f16(128, 32, BF16) | (1u << 15);   // A MN-major
     const uint32_t sa2 = tc::smem_u32(a2), sb2 = tc::smem_u32(smem + L.b2);
     uint64_t da2[2][2], db2[2];                        // tile pair 0; pair b is 2 b TILE further
 #pragma unroll
@@ -520,7 +564,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
 
 bool tcw_eligible(const TcArgs& ta) {
   const BeamArgs& a = ta.b;
-  return !ta.bf16 && !ta.split && ta.tw16 && a.nx == 4 && a.ny == 256 && a.mx == 4 &&
+  return !ta.split && ta.tw16 && a.nx == 4 && a.ny == 256 && a.mx == 4 &&
          a.my == 512 && a.nyf == 256 && a.ew_dft &&
          (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
 }
@@ -535,7 +579,8 @@ int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st) {
   // the others exits
   size_t smem = (size_t)L.total;
   if (smem < 77 * 1024) smem = 77 * 1024;
-  auto kern = a.real_w ? beams_tcw_kernel<true> : beams_tcw_kernel<false>;
+  auto kern = ta.bf16 ? (a.real_w ? beams_tcw_kernel<true, true> : beams_tcw_kernel<false, true>)
+                      : (a.real_w ? beams_tcw_kernel<true, false> : beams_tcw_kernel<false, false>);
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       cudaSharedmemCarveoutMaxShared));
@@ -547,18 +592,22 @@ int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- plan tables --
-// Stage matrices of the warp-specialised FP16 form, row-major [n][k] (n = output, k =
-// input), FP64 rounded once to FP16, and the W512 twiddle pairs:
+// Stage matrices of the warp-specialised 16-bit forms, row-major [n][k] (n = output, k =
+// input), FP64 rounded once to FP16 (or BF16 when bf16), and the W512 twiddle pairs:
 //   b1[n = co 32 + k1][k = ci 16 + n1]   W32^(n1 k1), planar in and out
 //   b2[n = co 16 + k2][k = ci 16 + n2]   W16^(n2 k2), planar in and out
 //   tw16[(n2 16 + j) 2 + {0, 1}]         (cos, cos) and (-sin, -sin) of 2 pi n2 k1 / 512 for
-//                                        k1 = 2j, 2j + 1, as half2
+//                                        k1 = 2j, 2j + 1, as 16-bit pairs
 // With W = C + iS (S = -sin): out_re = sum in_re C - in_im S, out_im = sum in_re S + in_im C.
-__global__ void tcw_tables_kernel(uint16_t* b1, uint16_t* b2, uint32_t* tw16) {
+__global__ void tcw_tables_kernel(uint16_t* b1, uint16_t* b2, uint32_t* tw16, bool bf16) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  auto h = [](double v) {
-    __half x = __float2half_rn((float)v);
-    return *reinterpret_cast<uint16_t*>(&x);
+  auto h = [bf16](double v) -> uint16_t {
+    if (bf16) {
+      const __nv_bfloat16 x = __double2bfloat16(v);
+      return *reinterpret_cast<const uint16_t*>(&x);
+    }
+    const __half x = __float2half_rn((float)v);
+    return *reinterpret_cast<const uint16_t*>(&x);
   };
   auto entry = [](int co, int ci, double c, double sp) {
     if (co == 0) return ci == 0 ? c : -sp;
@@ -588,8 +637,8 @@ __global__ void tcw_tables_kernel(uint16_t* b1, uint16_t* b2, uint32_t* tw16) {
   }
 }
 
-int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, cudaStream_t st) {
-  tcw_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, tw16);
+int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, bool bf16, cudaStream_t st) {
+  tcw_tables_kernel<<<(64 * 32 + 255) / 256, 256, 0, st>>>(b1, b2, tw16, bf16);
   FFTBF_CUDA_TRY(cudaGetLastError());
   return FFTBF_OK;
 }

@@ -151,13 +151,13 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
     rc = build_tc_tables_lo(p->d_b1lo, p->d_b2lo, 0);
     if (rc != FFTBF_OK) return rc;
   }
-  if (prec == FFTBF_PREC_TC_FP16) {
+  if (prec == FFTBF_PREC_TC_FP16 || prec == FFTBF_PREC_TC_BF16) {
     if (!p->d_b1w) {
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_b1w, sizeof(uint16_t) * 64 * 32));
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_b2w, sizeof(uint16_t) * 32 * 32));
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_tw16, sizeof(uint32_t) * 16 * 16 * 2));
     }
-    rc = build_tcw_tables(p->d_b1w, p->d_b2w, p->d_tw16, 0);
+    rc = build_tcw_tables(p->d_b1w, p->d_b2w, p->d_tw16, prec == FFTBF_PREC_TC_BF16, 0);
     if (rc != FFTBF_OK) return rc;
   }
   FFTBF_CUDA_TRY(cudaDeviceSynchronize());
@@ -222,7 +222,7 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
             (p->ny & 3) == 0 && a.nyf == p->ny;
     ta.b1lo = p->d_b1lo;
     ta.b2lo = p->d_b2lo;
-    if (p->precision == FFTBF_PREC_TC_FP16) {
+    if (p->precision == FFTBF_PREC_TC_FP16 || p->precision == FFTBF_PREC_TC_BF16) {
       ta.b1w = p->d_b1w;
       ta.b2w = p->d_b2w;
       ta.tw16 = p->d_tw16;

@@ -104,7 +104,7 @@ int build_tc_tables(uint16_t* b1, uint16_t* b2, bool bf16, cudaStream_t st);
 int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st);
 bool tcw_eligible(const TcArgs& ta);
 int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st);
-int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, cudaStream_t st);
+int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, bool bf16, cudaStream_t st);
 int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, int layout,
                          float* D, int* err, cudaStream_t st);
 int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st);

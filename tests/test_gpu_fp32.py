@@ -218,19 +218,19 @@ def test_tied_rejects_off_grid_pointing():
                                         ((3, 128, 3, 256, 2, 2, 32, 16), "fp32"),
                                         ((8, 64, 8, 128, 2, 2, 32, 16), "fp32"),
                                         ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16_serial"),
-                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_bf16"),
+                                        ((4, 256, 4, 512, 2, 2, 32, 16), "tc_bf16_serial"),
                                         ((4, 256, 4, 512, 2, 2, 32, 16), "tc_fp16x3")])
 def test_misaligned_voltages_give_identical_beams(shape, prec, monkeypatch):
     """A voltage pointer off the 16-byte boundary is accepted (staged byte by byte instead
     of with 16-byte copies) and gives bit-identical beams. The aligned call runs the
     constant-size instance of the 4x256 lattice (or of an exactly 2x-padded warp-path
     shape), the misaligned one the runtime-size instance, so this also checks that both
-    sum in the same order. (tc_fp16_serial: the serial tensor-core kernel, which serves
-    misaligned FP16 calls; aligned FP16 calls run the warp-specialised kernel, checked
-    against the oracle in test_misaligned_fp16_tensor_core_kernels_agree.)"""
-    if prec == "tc_fp16_serial":
+    sum in the same order. (tc_fp16_serial, tc_bf16_serial: the serial tensor-core kernel,
+    which serves misaligned FP16 and BF16 calls; aligned calls run the warp-specialised
+    kernel, checked against the oracle in test_misaligned_tensor_core_kernels_agree.)"""
+    if prec.endswith("_serial"):
         monkeypatch.setenv("FFTBF_TC_KERNEL", "serial")
-        prec = "tc_fp16"
+        prec = prec[:-len("_serial")]
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=77)
     flat = torch.from_numpy(np.ascontiguousarray(v).reshape(-1))
@@ -250,11 +250,12 @@ def test_misaligned_voltages_give_identical_beams(shape, prec, monkeypatch):
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_misaligned_fp16_tensor_core_kernels_agree():
-    """FP16 on the 4x256 lattice: an aligned voltage pointer runs the warp-specialised
-    tensor-core kernel (bulk copies need 16-byte alignment), a misaligned one the serial
-    kernel. Their roundings differ, so both are held to the FP16 form's bound against the
-    oracle (5e-3 of each beam) and to each other."""
+@pytest.mark.parametrize("form,tol", [("fp16", 5e-3), ("bf16", 3e-2)])
+def test_misaligned_tensor_core_kernels_agree(form, tol):
+    """FP16 or BF16 on the 4x256 lattice: an aligned voltage pointer runs the
+    warp-specialised tensor-core kernel (bulk copies need 16-byte alignment), a misaligned
+    one the serial kernel. Their roundings differ, so both are held to the form's bound
+    against the oracle (5e-3 or 3e-2 of each beam)."""
     shape = (4, 256, 4, 512, 2, 2, 32, 16)
     nx, ny, mx, my, npol, nfreq, T, n_int = shape
     v, w = make_case(nx, ny, mx, my, npol, nfreq, T, n_int, weights="half_sine", seed=78)
@@ -266,11 +267,11 @@ def test_misaligned_fp16_tensor_core_kernels_agree():
         base[off:off + flat.numel()].copy_(flat)
         out = torch.full((T // n_int, nfreq, mx, my), float("nan"), device="cuda")
         with fb.plan_create(nx, ny, mx, my, npol, nfreq, n_int, weights=w) as plan:
-            fb.plan_set_precision(plan, fb.PREC_TC_FP16)
+            fb.plan_set_precision(plan, fb.PREC_TC_FP16 if form == "fp16" else fb.PREC_TC_BF16)
             fb.execute(plan, base[off:off + flat.numel()], T, out)
             fb.plan_sync(plan)
         outs.append(out.cpu().numpy())
     for o in outs:
         assert np.all(np.isfinite(o))
-        assert (np.abs(o - ref) / ref).max() <= 5e-3
+        assert (np.abs(o - ref) / ref).max() <= tol
     assert (np.abs(outs[0] - outs[1]) / ref).max() <= 1e-2

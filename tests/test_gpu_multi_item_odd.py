@@ -64,8 +64,10 @@ def test_fp16_several_items_per_cta_odd_pairs(case, kern, monkeypatch):
     assert np.sqrt(np.mean(rel ** 2)) <= RMS_FP16, kern
 
 
-def test_bf16_several_items_per_cta_odd_pairs(case):
+@pytest.mark.parametrize("kern", ["ws", "serial"])
+def test_bf16_several_items_per_cta_odd_pairs(case, kern, monkeypatch):
     v, w, ref = case
+    monkeypatch.setenv("FFTBF_TC_KERNEL", kern)
     got = run(v, w, fb.PREC_TC_BF16)
     rel = np.abs(got - ref) / ref
     assert np.all(np.isfinite(got))

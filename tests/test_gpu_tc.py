@@ -103,23 +103,25 @@ def test_tc_serial_kernel_matches_pipelined(form, monkeypatch):
     assert np.array_equal(piped, serial), f"max rel diff {diff.max():.3e} at {np.argmax(diff)}"
 
 
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
 @pytest.mark.parametrize("wk", ["half_sine", "random"])
 @pytest.mark.parametrize("npol,n_int,T", [(2, 48, 96), (1, 5, 30), (2, 3, 12)],
                          ids=["2pol", "1pol-odd", "2pol-short"])
-def test_tc_fp16_kernels_agree_with_oracle(wk, npol, n_int, T, monkeypatch):
-    """The warp-specialised FP16 kernel (default for aligned 4x256 voltages) and the serial
-    FP16 kernel, each against the oracle at the FP16 bounds, on real and complex weights,
-    one or two polarisations and an odd snapshot count (a pair with one snapshot)."""
+def test_tc_16bit_kernels_agree_with_oracle(form, wk, npol, n_int, T, monkeypatch):
+    """The warp-specialised kernel (default for aligned 4x256 voltages) and the serial
+    kernel of the FP16 and BF16 forms, each against the oracle at the form's bounds, on
+    real and complex weights, one or two polarisations and an odd snapshot count (a pair
+    with one snapshot)."""
     shape = (4, 256, 4, 512, npol, 3, T, n_int)
     v, w = make_case(*shape, weights=wk, seed=9 + npol + n_int)
     ref = oracle_beams(v, w, 4, 256, 4, 512, npol, 3, n_int)
     for kern in ("ws", "serial"):
         monkeypatch.setenv("FFTBF_TC_KERNEL", kern)
-        got = run_tc(v, w, shape, "fp16")
+        got = run_tc(v, w, shape, form)
         rel = np.abs(got - ref) / ref
         assert np.all(np.isfinite(got)), kern
-        assert rel.max() <= TOL_TC["fp16"], (kern, rel.max())
-        assert np.sqrt(np.mean(rel ** 2)) <= RMS_TC["fp16"], kern
+        assert rel.max() <= TOL_TC[form], (kern, rel.max())
+        assert np.sqrt(np.mean(rel ** 2)) <= RMS_TC[form], kern
 
 
 def test_tc_bit_identical_alone_and_in_batch():
