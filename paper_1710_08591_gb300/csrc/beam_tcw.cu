@@ -9,7 +9,8 @@
 // (n = n2 + 16 n1, k = k1 + 32 k2; inputs with n1 >= 16 are the padding):
 //   stage 1 (tcgen05.mma, M=128 N=64 K=32): rows (snapshot s, E-W beam A, n2) of a snapshot
 //     pair, the pruned 32-point DFT over n1 as a real-embedded GEMM;
-//   twiddle: X1 *= W512^(n2 k1) while draining TMEM, in packed half arithmetic;
+//   twiddle: X1 *= W512^(n2 k1) while draining TMEM, in packed half arithmetic (FP32 for
+//     the BF16 form);
 //   stage 2 (tcgen05.mma, M=128 N=32 K=32 per snapshot): rows (A, k1), a 16-point DFT over
 //     n2 giving X[k1 + 32 k2]; the thread owning TMEM row (A, k1) squares it and integrates
 //     over time and polarisation in registers (Eq. bf).
