@@ -79,7 +79,6 @@ constexpr uint32_t TMEM_COLS = 64 * NT4;      // buffer t at columns 64 t: D1 of
 //   (m % 8) * 2 + (k % 8) * 16 + (m / 8) * SBO + (k / 8) * LBO
 constexpr int SBO = 128, LBO = 2048, TILE = 8192;
 constexpr int B_LBO = 128, B_SBO = 512;       // K-major DFT matrices
-constexpr int TWF_ROW = 17;                   // float4 per n2 row of the FP32 twiddles (padded)
 // RAWF per round stage; A1F, A1E per round parity (a round's two pairs use A1 tiles
 // 2 (k % 2), + 1); D1F, D1E, D2F, D2E per tensor-memory buffer; A2F, A2E per A2 tile pair
 enum { RAWF = 0, A1F = RAWF + RQ, A1E = A1F + 2, D1F = A1E + 2, D1E = D1F + NT4,
@@ -98,7 +97,7 @@ __host__ __device__ inline Smem layout() {
   L.b1 = take(64 * 32 * 2);
   L.b2 = take(32 * 32 * 2);
   L.w = take(2 * NANT * 2);              // FP16 weights: real part, then imaginary part
-  L.twf = take(16 * TWF_ROW * 16);       // FP32 twiddles of the BF16 form
+  L.twf = take(16 * 16 * 16);            // FP32 twiddles of the BF16 form, [j][n2] float4
   L.raw = take(R * 2 * NANT);
   L.bars = take(NBAR * 8);
   L.misc = take(16);
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
       for (int i = tid; i < 16 * 16; i += NT) {
         const int r = i >> 4, j = i & 15;
         const float2 w0 = a.tw[(r * 2 * j) & 511], w1 = a.tw[(r * (2 * j + 1)) & 511];
-        tw[r * TWF_ROW + j] = make_float4(w0.x, w1.x, w0.y, w1.y);
+        tw[j * 16 + r] = make_float4(w0.x, w1.x, w0.y, w1.y);
       }
     }
   }
@@ -375,9 +374,10 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
     const int lq = warp - 4;
     // twiddles W512^(n2 k1) of this row: FP16, half2 pairs over adjacent k1 (cos, then
     // -sin), in registers; BF16, FP32 quadruples (cos, cos, -sin, -sin) in shared memory
-    // (the twiddle is applied in FP32 and the product rounded once to BF16)
+    // (the twiddle is applied in FP32 and the product rounded once to BF16), laid out
+    // [j][n2] so that each half-warp's 16-byte loads read 256 contiguous bytes
     uint32_t ch[BF16 ? 1 : 16], dh[BF16 ? 1 : 16];
-    const float4* twf = reinterpret_cast<const float4*>(smem + L.twf) + n2 * TWF_ROW;
+    const float4* twf = reinterpret_cast<const float4*>(smem + L.twf) + n2;
     if constexpr (!BF16) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(tcw::NT, 2) beams_tcw_kernel(const TcArgs ta) 
             for (int jj = 0; jj < 4; ++jj) {
               const int jl = 4 * qq + jj, j = 4 * q + jj;
               if constexpr (BF16) {
-                const float4 w = twf[j];
+                const float4 w = twf[16 * j];
                 const float2 re = make_float2(__uint_as_float(xr[2 * jl]), __uint_as_float(xr[2 * jl + 1]));
                 const float2 im = make_float2(__uint_as_float(xi[2 * jl]), __uint_as_float(xi[2 * jl + 1]));
                 const float2 c = make_float2(w.x, w.y), d = make_float2(w.z, w.w);
