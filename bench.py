@@ -70,9 +70,9 @@ def flops_per_snapshot(nx, ny, mx, my):
 # whenever the kernel changes until it is captured again.
 TRAFFIC_FP32 = 16 * (403.222784e6 + 3.644416e6)
 # The same for the FP16 tensor-core form's beam kernel (`--profile-case --form tc_fp16`).
-TRAFFIC_TCW = 16 * (402.730240e6 + 6.111488e6)
+TRAFFIC_TCW = None
 # The beam kernel each tensor-core form launches on the 4x256 lattice
-TC_KERNEL = {"tc_fp16": "beams_tcw_kernel<true, false>", "tc_bf16": "beams_tcw_kernel<true, true>",
+TC_KERNEL = {"tc_fp16": "beams_tcg_kernel<true, false>", "tc_bf16": "beams_tcg_kernel<true, true>",
              "tc_fp16x3": "beams_tc_kernel<0, 1, 1>"}
 # The same for one batched step (one batch_kernel launch over 8192 samples), from the
 # 512-sample profile case (`--workload batched --profile-case`) scaled x16.

@@ -306,8 +306,12 @@ int fftbf_debug_unpack(const uint8_t* in_dev, int64_t n, float* out_dev, void* s
  * 16-bit operands (FP16, or BF16 if bf16 != 0), staged in the kernels' shared-memory
  * layouts: `padded` = 0 canonical K-major A, 1 K-major A with the padded strides of the
  * stage-2 operand, 2 MN-major A (element (m, k) at byte (m%8)*2 + (k%8)*16 + (m/8)*128 +
- * (k/8)*2048, the operand layout of the warp-specialised FP16 kernel); one pair of
- * tcgen05.mma instructions, FP32 accumulation in tensor memory. n = 32, 64, 128 or 256.
+ * (k/8)*2048, the operand layout of the warp-specialised FP16 kernel), 3 A in tensor
+ * memory (row m in lane m, two elements per 32-bit column, written by tcgen05.st) with
+ * K-major B, 4 canonical K-major A with MN-major B (element (n, k) at byte (n%8)*2 +
+ * (k%8)*16 + (n/8)*128 + (k/8)*16n); 3 and 4 are the operand forms of the grouped
+ * kernel and take n <= 128. One pair of tcgen05.mma instructions, FP32 accumulation in
+ * tensor memory. n = 32, 64, 128 or 256.
  * Device pointers, row-major. Synchronises `stream`; FFTBF_ETIMEOUT if the tensor core
  * did not complete within one second.
  */

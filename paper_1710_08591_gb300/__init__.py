@@ -454,7 +454,8 @@ def debug_wait_timeout(limit_us: int, stream=None) -> int:
 
 def debug_tc_gemm(a, b, n: int, bf16: bool, padded: int, d, stream=None) -> None:
     """D[128][n] = A[128][32] B[n][32]^T on the tensor cores (test hook). padded: 0 K-major
-    A, 1 K-major A with the stage-2 operand's padded strides, 2 MN-major A."""
+    A, 1 K-major A with the stage-2 operand's padded strides, 2 MN-major A, 3 A in tensor
+    memory, 4 MN-major B (3 and 4: n <= 128)."""
     _check(lib().fftbf_debug_tc_gemm(_dptr(a), _dptr(b), int(n), int(bool(bf16)), int(padded),
                                      _dptr(d), _stream(stream)))
 

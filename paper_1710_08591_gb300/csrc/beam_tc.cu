@@ -868,13 +868,17 @@ int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st) {
   const BeamArgs& a = ta.b;
   if (a.nwin <= 0) return FFTBF_OK;
   const int64_t items = a.nwin * a.nfreq;
-  // FP16 and BF16 on the 4x256 lattice: the warp-specialised kernel with MN-major planar
-  // operands (beam_tcw.cu) unless FFTBF_TC_KERNEL=serial or FFTBF_TC_PIPE=1 ask for the
-  // kernels below. Of those two, the serial kernel (several CTAs per SM, every warp in every phase)
-  // measures faster than the first warp-specialised pipeline on the 4x256 lattice.
+  // FP16 and BF16 on the 4x256 lattice: the grouped kernel (four snapshots per stage-1 MMA,
+  // intermediates in tensor memory; beam_tcg.cu), or with FFTBF_TC_KERNEL=ws the pair-wise
+  // warp-specialised kernel with MN-major planar operands (beam_tcw.cu), unless
+  // FFTBF_TC_KERNEL=serial or FFTBF_TC_PIPE=1 ask for the kernels below. Of those two, the
+  // serial kernel (several CTAs per SM, every warp in every phase) measures faster than the
+  // first warp-specialised pipeline on the 4x256 lattice.
   const char* pipe = getenv("FFTBF_TC_PIPE");
   const char* which = getenv("FFTBF_TC_KERNEL");
   const bool old_kernel = (pipe && pipe[0] && pipe[0] != '0') || (which && which[0] == 's');
+  const bool pairwise = which && which[0] == 'w';
+  if (!old_kernel && !pairwise && tcg_eligible(ta)) return launch_beams_tcg(ta, nsm, st);
   if (!old_kernel && tcw_eligible(ta)) {
     TcArgs tw = ta;
     tw.b1 = ta.b1w;
@@ -981,15 +985,20 @@ int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st) {
 // ------------------------------------------------------------ GEMM test hook --
 // D[128][n] = A[128][32] * B[n][32]^T with 16-bit operands (FP16 or BF16) in the
 // canonical layout (A's strides padded like the stage-2 operand if `padded`), one MMA
-// pair, FP32 in TMEM, read back with tcgen05.ld.
+// pair, FP32 in TMEM, read back with tcgen05.ld. Layout 3 puts A in tensor memory (row m
+// in lane m, two elements per column, written with tcgen05.st) and layout 4 stores B
+// MN-major, the two operand forms of the grouped kernel.
 template <bool BF16>
 __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A, const uint16_t* B,
                                                                 int n, int padded, float* D, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* smem = smem_tc;
   // padded: 0 canonical K-major A, 1 K-major with the stage-2 operand's padded strides,
-  // 2 MN-major A (element (m, k) at (m%8)*2 + (k%8)*16 + (m/8)*128 + (k/8)*2048)
-  const bool mn = padded == 2;
+  // 2 MN-major A (element (m, k) at (m%8)*2 + (k%8)*16 + (m/8)*128 + (k/8)*2048),
+  // 3 A in tensor memory (columns 224..239), 4 canonical A and MN-major B (element (n, k)
+  // at (n%8)*2 + (k%8)*16 + (n/8)*128 + (k/8)*16n)
+  const bool mn = padded == 2, a_tmem = padded == 3, b_mn = padded == 4;
+  if (padded > 2) padded = 0;
   const int albo = mn ? 2048 : (padded ? tcl::A2_LBO : tcl::A1_LBO);
   const int asbo = mn ? 128 : (padded ? tcl::A2_SBO : tcl::A1_SBO);
   unsigned char* as = smem;
@@ -1011,21 +1020,42 @@ __global__ void __launch_bounds__(128, 1) debug_tc_gemm_kernel(const uint16_t* A
       *reinterpret_cast<uint16_t*>(as + (m & 7) * 2 + (k & 7) * 16 + (m >> 3) * asbo + (k >> 3) * albo) =
           A[m * 32 + k];
     }
-  } else {
+  } else if (!a_tmem) {
     load_kmajor(as, A, 128, albo, asbo, tid, 128);
   }
-  load_kmajor(bs, B, n, tcl::B_LBO, tcl::B_SBO, tid, 128);
+  const int blbo = b_mn ? 16 * n : tcl::B_LBO, bsbo = b_mn ? 128 : tcl::B_SBO;
+  if (b_mn) {
+    for (int i = tid; i < n * 32; i += 128) {
+      const int m = i >> 5, k = i & 31;
+      *reinterpret_cast<uint16_t*>(bs + (m & 7) * 2 + (k & 7) * 16 + (m >> 3) * bsbo + (k >> 3) * blbo) =
+          B[m * 32 + k];
+    }
+  } else {
+    load_kmajor(bs, B, n, tcl::B_LBO, tcl::B_SBO, tid, 128);
+  }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *taddr_sm;
+  if (a_tmem) {
+    uint32_t r[16];
+    for (int j = 0; j < 16; ++j) r[j] = (uint32_t)A[tid * 32 + 2 * j] | ((uint32_t)A[tid * 32 + 2 * j + 1] << 16);
+    tc::tmem_st16(tbase + ((uint32_t)(32 * warp) << 16) + 224, r);
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
   if (tid == 0) {
-    const uint32_t id = tc::idesc_f16(128, n, BF16) | (mn ? (1u << 15) : 0u);   // A MN-major
-    for (int kk = 0; kk < 2; ++kk)
-      tc::mma_f16(tbase, tc::smem_desc(tc::smem_u32(as) + kk * 2 * albo, albo, asbo),
-                  tc::smem_desc(tc::smem_u32(bs) + kk * 2 * tcl::B_LBO, tcl::B_LBO, tcl::B_SBO),
-                  id, kk);
+    const uint32_t id = tc::idesc_f16(128, n, BF16) | (mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u);
+    for (int kk = 0; kk < 2; ++kk) {
+      const uint64_t bd = tc::smem_desc(tc::smem_u32(bs) + kk * 2 * blbo, blbo, bsbo);
+      if (a_tmem)
+        tc::mma_f16_ts(tbase, tbase + 224 + 8 * kk, bd, id, kk);
+      else
+        tc::mma_f16(tbase, tc::smem_desc(tc::smem_u32(as) + kk * 2 * albo, albo, asbo), bd, id, kk);
+    }
     tc::mma_commit(bar);
   }
   const bool ok = __syncthreads_and(tc::mbar_wait(bar, 0, tcl::WAIT_NS));
@@ -1068,6 +1098,7 @@ int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16,
                          float* D, int* err, cudaStream_t st) {
   const bool padded = layout == 1;
   const int asbo = padded ? tcl::A2_SBO : tcl::A1_SBO;
+  if (layout > 2 && n > 128) return set_error(FFTBF_EINVAL, "layouts 3 and 4 take n <= 128");
   const size_t smem = (layout == 2 ? 8192 : 16 * asbo) + (n / 8) * tcl::B_SBO + 64;
   auto kern = bf16 ? debug_tc_gemm_kernel<true> : debug_tc_gemm_kernel<false>;
   FFTBF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -156,8 +156,11 @@ int fftbf_plan_set_precision(fftbf_plan* p, int prec) {
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_b1w, sizeof(uint16_t) * 64 * 32));
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_b2w, sizeof(uint16_t) * 32 * 32));
       FFTBF_CUDA_TRY(cudaMalloc(&p->d_tw16, sizeof(uint32_t) * 16 * 16 * 2));
+      FFTBF_CUDA_TRY(cudaMalloc(&p->d_f1, sizeof(uint16_t) * 128 * 128));
     }
     rc = build_tcw_tables(p->d_b1w, p->d_b2w, p->d_tw16, prec == FFTBF_PREC_TC_BF16, 0);
+    if (rc != FFTBF_OK) return rc;
+    rc = build_tcg_table(p->d_f1, prec == FFTBF_PREC_TC_BF16, 0);
     if (rc != FFTBF_OK) return rc;
   }
   FFTBF_CUDA_TRY(cudaDeviceSynchronize());
@@ -226,6 +229,7 @@ int fftbf_execute(fftbf_plan* p, const uint8_t* volts, int64_t T, float* beams, 
       ta.b1w = p->d_b1w;
       ta.b2w = p->d_b2w;
       ta.tw16 = p->d_tw16;
+      ta.f1 = p->d_f1;
     }
     rc = launch_beams_tc(ta, p->nsm, st);
   }
@@ -320,6 +324,7 @@ void fftbf_destroy(fftbf_plan* p) {
     cudaFree(p->d_b1w);
     cudaFree(p->d_b2w);
     cudaFree(p->d_tw16);
+    cudaFree(p->d_f1);
     cudaFree(p->d_err);
   }
   delete p;
@@ -357,9 +362,9 @@ int fftbf_debug_tc_gemm(const uint16_t* a, const uint16_t* b, int n, int bf16, i
   int* err = nullptr;
   FFTBF_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
   cudaMemsetAsync(err, 0, sizeof(int), st);
-  if (padded < 0 || padded > 2) {
+  if (padded < 0 || padded > 4) {
     cudaFree(err);
-    return set_error(FFTBF_EINVAL, "layout must be 0, 1 or 2");
+    return set_error(FFTBF_EINVAL, "layout must be 0 to 4");
   }
   int rc = launch_debug_tc_gemm(a, b, n, bf16 != 0, padded, d, err, st);
   int h = 0;

@@ -97,6 +97,9 @@ struct TcArgs {
   const uint16_t* b1w;  // [64][32]
   const uint16_t* b2w;  // [32][32]
   const uint32_t* tw16; // [16 n2][16 k1 pairs][2] half2 (cos, -sin)
+  // grouped kernel (4x256 lattice): E-W x pruned W32 stage matrix [128][128] (b2w is its
+  // stage-2 matrix)
+  const uint16_t* f1;
 };
 bool tc_supported(int nx, int ny, int mx, int my);
 int launch_beams_tc(const TcArgs& ta, int nsm, cudaStream_t st);
@@ -105,6 +108,9 @@ int build_tc_tables_lo(uint16_t* b1, uint16_t* b2, cudaStream_t st);
 bool tcw_eligible(const TcArgs& ta);
 int launch_beams_tcw(const TcArgs& ta, int nsm, cudaStream_t st);
 int build_tcw_tables(uint16_t* b1, uint16_t* b2, uint32_t* tw16, bool bf16, cudaStream_t st);
+bool tcg_eligible(const TcArgs& ta);
+int launch_beams_tcg(const TcArgs& ta, int nsm, cudaStream_t st);
+int build_tcg_table(uint16_t* f1, bool bf16, cudaStream_t st);
 int launch_debug_tc_gemm(const uint16_t* A, const uint16_t* B, int n, bool bf16, int layout,
                          float* D, int* err, cudaStream_t st);
 int launch_debug_wait_timeout(uint64_t limit_ns, int* err, cudaStream_t st);
@@ -206,6 +212,7 @@ struct fftbf_plan {
   uint16_t* d_b1w = nullptr;      // warp-specialised FP16 kernel: planar stage matrices
   uint16_t* d_b2w = nullptr;
   uint32_t* d_tw16 = nullptr;     // and its W512 twiddle pairs
+  uint16_t* d_f1 = nullptr;       // grouped FP16/BF16 kernel: E-W x W32 stage matrix
   float tc_scale = 1.f;
   int* d_err = nullptr;           // device error word of bounded waits
   std::vector<cudaStream_t> streams_used;

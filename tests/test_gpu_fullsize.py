@@ -132,19 +132,23 @@ def test_tied_slice(run, j, f):
     assert err.max() <= TOL_BEAM, f"max scaled err {err.max():.3g}"
 
 
-FORMS = [("fp16", False), ("bf16", False), ("fp16x3", False), ("fp16", True), ("bf16", True)]
+FORMS = [("fp16", None), ("bf16", None), ("fp16x3", None), ("fp16", "ws"), ("bf16", "ws"),
+         ("fp16", "pipe"), ("bf16", "pipe")]
 
 
 @pytest.mark.parametrize("form,pipe", FORMS,
-                         ids=["fp16", "bf16", "fp16x3", "fp16-pipe", "bf16-pipe"])
+                         ids=["fp16", "bf16", "fp16x3", "fp16-ws", "bf16-ws", "fp16-pipe", "bf16-pipe"])
 def test_tensor_core_form_full_size(run, form, pipe, monkeypatch):
     """A tensor-core form over the bench's 8192-item launch: sampled slices against the
     oracle, every item against the FP32 form's beams (both within the form's per-beam
     bound of the oracle) and against Parseval."""
-    if pipe:
+    monkeypatch.delenv("FFTBF_TC_KERNEL", raising=False)
+    if pipe == "pipe":
         monkeypatch.setenv("FFTBF_TC_PIPE", "1")
     else:
         monkeypatch.delenv("FFTBF_TC_PIPE", raising=False)
+        if pipe == "ws":
+            monkeypatch.setenv("FFTBF_TC_KERNEL", "ws")
     prec = {"fp16": fb.PREC_TC_FP16, "bf16": fb.PREC_TC_BF16, "fp16x3": fb.PREC_TC_FP16X3}[form]
     beams = torch.full((NWIN, NFREQ, MX, MY), float("nan"), device="cuda")
     with fb.plan_create(NX, NY, MX, MY, NPOL, NFREQ, NINT, weights=run["w"]) as plan:
@@ -165,7 +169,7 @@ def test_tensor_core_form_full_size(run, form, pipe, monkeypatch):
     tot = got.astype(np.float64).sum(axis=(-2, -1))
     pref = run["parseval"][np.arange(NWIN) % (T_HOST // NINT)]
     prel = np.abs(tot - pref) / pref
-    print(f"\n[full-size {form}{' pipe' if pipe else ''}] oracle slices: max rel "
+    print(f"\n[full-size {form}{' ' + pipe if pipe else ''}] oracle slices: max rel "
           f"{max(x[0] for x in worst):.3e}, rms {max(x[1] for x in worst):.3e}; every item vs "
           f"FP32 form: max rel {rel_all.max():.3e}, rms {np.sqrt(np.mean(rel_all ** 2)):.3e}; "
           f"Parseval max rel {prel.max():.3e}")

@@ -4,10 +4,12 @@ snapshot counts, against the FP64 oracle (Eq. fftbeamform, Eq. bf).
 One polarisation and n_int = 5 give 5 snapshots per (window, channel) item: the FP32
 kernel's last iteration of every item holds a single snapshot, and the tensor-core kernels'
 last snapshot pair of every item holds one. With 2 windows x 400 channels = 800 items, the
-CTAs of the FP32 kernel (4 per SM) and of the tensor-core kernels (2 per SM) each take
+CTAs of the FP32 kernel (4 per SM) and of the tensor-core kernels (1 or 2 per SM) each take
 several items in turn; in the warp-specialised FP16 kernel, whose input warps work on two
 pairs per round, a CTA with 3 items has 9 pairs, so rounds straddle item boundaries and the
-last round holds one pair."""
+last round holds one pair; in the grouped kernel (four snapshots per group, one CTA per
+SM) a CTA with 5 or 6 items has 25 or 30 snapshots, so groups straddle items and the last
+group holds one or two snapshots."""
 import numpy as np
 import pytest
 
@@ -53,7 +55,7 @@ def test_fp32_several_items_per_cta_odd_snapshots(case):
     assert rel_err_per_beam(got, ref).max() <= TOL_BEAM
 
 
-@pytest.mark.parametrize("kern", ["ws", "serial"])
+@pytest.mark.parametrize("kern", ["grouped", "ws", "serial"])
 def test_fp16_several_items_per_cta_odd_pairs(case, kern, monkeypatch):
     v, w, ref = case
     monkeypatch.setenv("FFTBF_TC_KERNEL", kern)
@@ -64,7 +66,7 @@ def test_fp16_several_items_per_cta_odd_pairs(case, kern, monkeypatch):
     assert np.sqrt(np.mean(rel ** 2)) <= RMS_FP16, kern
 
 
-@pytest.mark.parametrize("kern", ["ws", "serial"])
+@pytest.mark.parametrize("kern", ["grouped", "ws", "serial"])
 def test_bf16_several_items_per_cta_odd_pairs(case, kern, monkeypatch):
     v, w, ref = case
     monkeypatch.setenv("FFTBF_TC_KERNEL", kern)

@@ -31,7 +31,7 @@ def _lib():
 
 
 @pytest.mark.parametrize("bf16", [False, True], ids=["fp16", "bf16"])
-@pytest.mark.parametrize("padded", [0, 1, 2], ids=["canon", "padded", "mn-major"])
+@pytest.mark.parametrize("padded", [0, 1, 2, 3, 4], ids=["canon", "padded", "mn-major", "a-tmem", "b-mn-major"])
 @pytest.mark.parametrize("n", [32, 64, 128])
 def test_tc_gemm_building_block(bf16, padded, n):
     rng = np.random.default_rng(n + 2 * padded + bf16)
@@ -108,14 +108,15 @@ def test_tc_serial_kernel_matches_pipelined(form, monkeypatch):
 @pytest.mark.parametrize("npol,n_int,T", [(2, 48, 96), (1, 5, 30), (2, 3, 12)],
                          ids=["2pol", "1pol-odd", "2pol-short"])
 def test_tc_16bit_kernels_agree_with_oracle(form, wk, npol, n_int, T, monkeypatch):
-    """The warp-specialised kernel (default for aligned 4x256 voltages) and the serial
-    kernel of the FP16 and BF16 forms, each against the oracle at the form's bounds, on
+    """The grouped kernel (default for aligned 4x256 voltages), the pair-wise
+    warp-specialised kernel and the serial kernel of the FP16 and BF16 forms, each against
+    the oracle at the form's bounds, on
     real and complex weights, one or two polarisations and an odd snapshot count (a pair
     with one snapshot)."""
     shape = (4, 256, 4, 512, npol, 3, T, n_int)
     v, w = make_case(*shape, weights=wk, seed=9 + npol + n_int)
     ref = oracle_beams(v, w, 4, 256, 4, 512, npol, 3, n_int)
-    for kern in ("ws", "serial"):
+    for kern in ("grouped", "ws", "serial"):
         monkeypatch.setenv("FFTBF_TC_KERNEL", kern)
         got = run_tc(v, w, shape, form)
         rel = np.abs(got - ref) / ref
