@@ -70,7 +70,7 @@ def flops_per_snapshot(nx, ny, mx, my):
 # whenever the kernel changes until it is captured again.
 TRAFFIC_FP32 = 16 * (403.222784e6 + 3.644416e6)
 # The same for the FP16 tensor-core form's beam kernel (`--profile-case --form tc_fp16`).
-TRAFFIC_TCW = None
+TRAFFIC_TCW = 16 * (402.823680e6 + 6.055680e6)
 # The beam kernel each tensor-core form launches on the 4x256 lattice
 TC_KERNEL = {"tc_fp16": "beams_tcg_kernel<true, false>", "tc_bf16": "beams_tcg_kernel<true, true>",
              "tc_fp16x3": "beams_tc_kernel<0, 1, 1>"}
