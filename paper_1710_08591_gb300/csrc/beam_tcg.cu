@@ -340,14 +340,6 @@ __global__ void __launch_bounds__(tcg::NT, 1) beams_tcg_kernel(const TcArgs ta) 
       // ========================================== stage-1 MMAs
       const uint32_t id1 = tc::idesc_f16(128, 128, BF16) | (1u << 16);   // B MN-major
       const uint32_t sf1 = tc::smem_u32(smem + L.f1), sb1 = tc::smem_u32(b1);
-      // descriptors of the eight K steps (B: tile 0; tile b starts b B1_TILE bytes further,
-      // and the start-address field holds the address / 16)
-      uint64_t da[8], db[8];
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        da[kk] = tc::smem_desc(sf1 + kk * 2 * F1_LBO, F1_LBO, F1_SBO);
-        db[kk] = tc::smem_desc(sb1 + kk * 2 * B1_LBO, B1_LBO, B1_SBO);
-      }
       int64_t k = 0;
       for (; k < ngroups; ++k) {
         const int b = (int)(k % NB), d = (int)(k % ND);
