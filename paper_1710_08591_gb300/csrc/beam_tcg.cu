@@ -195,12 +195,19 @@ __global__ void __launch_bounds__(tcg::NT, 1) beams_tcg_kernel(const TcArgs ta) 
     const int iy0 = 16 * n1 + 8 * h;                   // feeds (ix, iy0 .. iy0 + 7)
     // weights x scale / 16 (the unpacked voltages carry a factor 16), half2 over feed pairs
     uint32_t wr[4], wi[4];
+    // BF16 form with real weights: the weights x scale as BF16 hi + lo parts, for voltages
+    // unpacked straight to BF16 (no factor 16)
+    __nv_bfloat162 wbh[4], wbl[4];
     const float sc = ta.scale * 0.0625f;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       const float2 w0 = a.w[ix * 256 + iy0 + 2 * p], w1 = a.w[ix * 256 + iy0 + 2 * p + 1];
       wr[p] = u32(__halves2half2(__float2half_rn(w0.x * sc), __float2half_rn(w1.x * sc)));
       wi[p] = u32(__halves2half2(__float2half_rn(w0.y * sc), __float2half_rn(w1.y * sc)));
+      const float2 wf = make_float2(w0.x * ta.scale, w1.x * ta.scale);
+      wbh[p] = __float22bfloat162_rn(wf);
+      const float2 hf = __bfloat1622float2(wbh[p]);
+      wbl[p] = __float22bfloat162_rn(make_float2(wf.x - hf.x, wf.y - hf.y));
     }
     // byte offsets: raw (snapshot-relative) and B operand (k = 32 ix + 16 ci + n1,
     // n = 32 g + 16 co + 8 h + j); a quarter-warp's 16-byte stores fill 128 bytes
@@ -221,6 +228,22 @@ __global__ void __launch_bounds__(tcg::NT, 1) beams_tcg_kernel(const TcArgs ta) 
           uint32_t zr[4], zi[4];
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
+            if constexpr (BF16 && REALW) {
+              // straight to BF16: each nibble, sign bit flipped, in the mantissa of 128 (ulp
+              // 1), minus 136 leaves it exactly; the weight as hi + lo with one rounding of
+              // re w_hi + (re w_lo)
+              const uint32_t t = __byte_perm(p < 2 ? wd.x : wd.y, 0u, (p & 1) ? 0x4342u : 0x4140u);
+              uint32_t ur = ((t >> 4) & 0x000F000Fu) ^ 0x43084308u, ui = (t & 0x000F000Fu) ^ 0x43084308u;
+              const uint32_t k136 = 0x43084308u;
+              const __nv_bfloat162 c136 = *reinterpret_cast<const __nv_bfloat162*>(&k136);
+              const __nv_bfloat162 re = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&ur), c136);
+              const __nv_bfloat162 im = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&ui), c136);
+              const __nv_bfloat162 br = __hfma2(re, wbh[p], __hmul2_rn(re, wbl[p]));
+              const __nv_bfloat162 bi = __hfma2(im, wbh[p], __hmul2_rn(im, wbl[p]));
+              zr[p] = *reinterpret_cast<const uint32_t*>(&br);
+              zi[p] = *reinterpret_cast<const uint32_t*>(&bi);
+              continue;
+            }
             // bytes of feeds 2p, 2p + 1 beside 0x64 bytes: [0x64 b1 0x64 b0]
             const uint32_t t = __byte_perm(p < 2 ? wd.x : wd.y, 0x64646464u, (p & 1) ? 0x4342u : 0x4140u);
             const __half2 re = __hsub2(h2((t & 0xFFF0FFF0u) ^ 0x00800080u), h2(0x64806480u));
