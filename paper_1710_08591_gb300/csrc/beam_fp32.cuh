@@ -109,10 +109,13 @@ template <> struct Dft<16> {
     }
     const float2 w[10] = {{1.f, 0.f}, {c1, -s1}, {kRs2, -kRs2}, {s1, -c1}, {0.f, -1.f},
                           {-s1, -c1}, {-kRs2, -kRs2}, {-c1, -s1}, {-1.f, 0.f}, {-c1, s1}};
+    // W16^4 = -i is a swap (the complex multiply by (0, -1) gives the same values up to the
+    // sign of a zero, which no later sum or square can turn into a different magnitude)
 #pragma unroll
     for (int n2 = 1; n2 < 4; ++n2)
 #pragma unroll
-      for (int k1 = 1; k1 < 4; ++k1) a[n2][k1] = cmul(a[n2][k1], w[n2 * k1]);
+      for (int k1 = 1; k1 < 4; ++k1)
+        a[n2][k1] = n2 * k1 == 4 ? mul_mi(a[n2][k1]) : cmul(a[n2][k1], w[n2 * k1]);
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
       float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(f4x256::NT, 4) beams_fp32_4x256_kernel(const B
 #pragma unroll
       for (int n1 = 0; n1 < 16; ++n1) x[n1] = xe[n1] = p1[n2 + kRow * n1];
 #pragma unroll
-      for (int n1 = 1; n1 < 16; ++n1) x[n1] = cmul(x[n1], w32(n1));
+      for (int n1 = 1; n1 < 16; ++n1) x[n1] = n1 == 8 ? mul_mi(x[n1]) : cmul(x[n1], w32(n1));   // W32^8 = -i
       Dft<16>::run(x);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(f4x256::NT, 4) beams_fp32_4x256_kernel(const B
       }
       __syncwarp();                                   // every lane's inputs read: rows 0..15 may change
       Dft<16>::run(xe);
+      p1[n2] = xe[0];                                 // k1 = 0: W512^0 = 1
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
+      for (int m = 1; m < 16; ++m) {
         const int k1 = 2 * m;
         p1[x1_row(k1) * kRow + n2] = cmul(xe[m], tw512[k1 * 16 + n2]);
       }
