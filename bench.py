@@ -68,7 +68,7 @@ def flops_per_snapshot(nx, ny, mx, my):
 # DRAM bytes (read + write) of one beam-kernel launch, from an ncu capture of the
 # 256-channel profile case scaled by snapshots to the 3072 x 1024 launch; set to None
 # whenever the kernel changes until it is captured again.
-TRAFFIC_FP32 = None
+TRAFFIC_FP32 = 16 * (402.845440e6 + 3.619840e6)
 # The same for the FP16 tensor-core form's beam kernel (`--profile-case --form tc_fp16`).
 TRAFFIC_TCW = 16 * (402.823680e6 + 6.055680e6)
 # The beam kernel each tensor-core form launches on the 4x256 lattice

@@ -46,7 +46,10 @@ __device__ __forceinline__ float nib(unsigned n) {
   return __int_as_float(0x4B000000u | (n ^ 8u)) - 8388616.0f;
 }
 __device__ __forceinline__ float2 unpack_byte(unsigned b) {
-  return make_float2(nib((b >> 4) & 15u), nib(b & 15u));
+  // both nibbles' subtractions as one packed add (the same roundings: exact)
+  return __fadd2_rn(make_float2(__int_as_float(0x4B000000u | (((b >> 4) & 15u) ^ 8u)),
+                                __int_as_float(0x4B000000u | ((b & 15u) ^ 8u))),
+                    make_float2(-8388616.0f, -8388616.0f));
 }
 
 // ------------------------------------------------------ forward DFTs in registers --

@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(f4x256::NT, 4) beams_fp32_4x256_kernel(const B
         for (int ix = 0; ix < 4; ++ix) {
           const unsigned v = *reinterpret_cast<const uint16_t*>(raw + s * NANT + ix * 256 + iy);
           const float2 x0 = unpack_byte(v & 255u), x1 = unpack_byte(v >> 8);
-          if constexpr (REALW) {
-            z0[ix] = make_float2(w0[ix].x * x0.x, w0[ix].x * x0.y);
-            z1[ix] = make_float2(w1[ix].x * x1.x, w1[ix].x * x1.y);
+          if constexpr (REALW) {                      // one packed multiply per feed
+            z0[ix] = __fmul2_rn(make_float2(w0[ix].x, w0[ix].x), x0);
+            z1[ix] = __fmul2_rn(make_float2(w1[ix].x, w1[ix].x), x1);
           } else {
             z0[ix] = cmul(w0[ix], x0);
             z1[ix] = cmul(w1[ix], x1);
