@@ -124,13 +124,13 @@ beams_fp32_n512_kernel(const BeamArgs a) {
         if constexpr (MX == 1 || MX == 2 || MX == 4 || MX == 8) {
           if (a.ew_dft) {
             if (a.real_w) {
-              // real weights: w x in two multiplies (the same roundings as the complex
-              // product with a zero imaginary part)
+              // real weights: w x in one packed multiply (the same roundings as the
+              // complex product with a zero imaginary part)
 #pragma unroll
               for (int ix = 0; ix < MX; ++ix) {
                 const float wr = wsm[ix * ny + iy].x;
                 const float2 xv = unpack_byte(rs[ix * ny + iy]);
-                z[ix] = make_float2(wr * xv.x, wr * xv.y);
+                z[ix] = __fmul2_rn(make_float2(wr, wr), xv);
               }
             } else {
 #pragma unroll

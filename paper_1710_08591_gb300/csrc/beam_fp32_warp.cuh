@@ -93,11 +93,11 @@ __host__ __device__ inline bool warp_full(const BeamArgs& a, int nh) {
          (reinterpret_cast<uintptr_t>(a.volts) & 15) == 0;
 }
 
-// Weight x unpacked byte; real weights in two multiplies (the same roundings as the complex
-// product with a zero imaginary part).
+// Weight x unpacked byte; real weights in one packed multiply of both parts (the same
+// roundings as the complex product with a zero imaginary part).
 __device__ __forceinline__ float2 weigh(bool real_w, float2 w, uint8_t b) {
   const float2 x = unpack_byte(b);
-  return real_w ? make_float2(w.x * x.x, w.x * x.y) : cmul(w, x);
+  return real_w ? __fmul2_rn(make_float2(w.x, w.x), x) : cmul(w, x);
 }
 
 // Unpack x weight and E-W transform of S snapshots into per-transform regions:

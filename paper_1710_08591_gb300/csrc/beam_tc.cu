@@ -331,12 +331,12 @@ beams_tc_kernel(const TcArgs ta) {
         const unsigned char* rs = raw + s * nant;
         if (NY256 || a.ew_dft) {
           if (a.real_w) {
-            // real weights: two multiplies, the same roundings as the complex product
+            // real weights: one packed multiply, the same roundings as the complex product
 #pragma unroll
             for (int ix = 0; ix < 4; ++ix) {
               const float wr = wsm[ix * ny + iy].x;
               const float2 xv = unpack_byte(rs[ix * ny + iy]);
-              z[ix] = make_float2(wr * xv.x, wr * xv.y);
+              z[ix] = __fmul2_rn(make_float2(wr, wr), xv);
             }
           } else {
 #pragma unroll
