@@ -76,7 +76,7 @@ TC_KERNEL = {"tc_fp16": "beams_tcg_kernel<true, false>", "tc_bf16": "beams_tcg_k
              "tc_fp16x3": "beams_tc_kernel<0, 1, 1>"}
 # The same for one batched step (one batch_kernel launch over 8192 samples), from the
 # 512-sample profile case (`--workload batched --profile-case`) scaled x16.
-TRAFFIC_BATCH = 16 * (2184.420e6 + 36.285184e6)
+TRAFFIC_BATCH = 16 * (2184.573696e6 + 36.063232e6)
 
 
 def samples_per_step():
