@@ -87,7 +87,12 @@ fftbf_plan* fftbf_plan_create(int nx, int ny, int pad_x, int pad_y, int npol, in
  * removes the scale from the result. FFTBF_PREC_TC_FP16X3 splits every operand into an
  * FP16 value and its FP16 residual (hi + lo) and forms each stage as hi*hi + hi*lo +
  * lo*hi in FP32, so the result has FP32 accuracy (the dropped lo*lo term is ~2^-22 of
- * each product). Call before fftbf_execute; not thread-safe with it.
+ * each product). On the 4x256 lattice with 16-byte aligned voltages the FP16 and BF16
+ * forms run a kernel that folds the E-W DFT into the first stage and keeps the second
+ * stage's operand in tensor memory; the environment variable FFTBF_TC_KERNEL=ws selects
+ * the pair-wise kernel (E-W DFT on the CUDA cores) instead and FFTBF_TC_KERNEL=serial the
+ * kernel every other shape uses; all three compute the same beams within the form's
+ * error. Call before fftbf_execute; not thread-safe with it.
  */
 int fftbf_plan_set_precision(fftbf_plan* plan, int precision);
 
